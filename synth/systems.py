@@ -1,0 +1,520 @@
+"""Synthetic gapped Kohn-Sham systems on uniform finite-difference grids.
+
+Recipe (stated here so the inputs can be rebuilt from seeds alone):
+
+* Grid: ``n = (nx, ny, nz)`` points, x fastest (flat index ``ix + nx*(iy + ny*iz)``).
+  A periodic axis of length L has spacing ``h = L/n`` and points ``i*h``; a Dirichlet axis
+  has ``h = L/(n+1)`` and points ``(i+1)*h`` (zero values on the two walls).
+* Local potential: a sum of Gaussian wells ``-D_a exp(-|r-R_a|^2 / (2 sigma^2))``; periodic
+  axes sum the 27 nearest periodic images so the potential is smooth across the cell.
+* Nonlocal projectors (Si-like cells): per atom one s-type and three p-type Gaussians
+  (``exp(-d^2/(2 sp^2))`` times 1, dx, dy, dz; sp = 1.1 bohr), truncated at
+  ``|d| <= 3.5 sp``, normalised so that ``dV * sum chi^2 = 1``;
+  ``V_nl = sum_l gamma_l chi_l chi_l^T dV``.  The s channel is repulsive
+  (gamma ~ U[1.5, 2.5] Ha) and the p channels attractive (gamma ~ U[-3.5, -2.5] Ha): this
+  brings the on-site s and p levels together, so that sp3-like bonding opens a gap after
+  two states per atom (four valence electrons per atom, as in Si).  The four projectors of
+  one atom share one support and form one :class:`ProjectorGroup`.
+* Atom positions of the Si-like cells: diamond sites of a cubic cell, each moved by
+  ``delta * r_i`` with ``delta`` = 10% of the nearest-neighbour distance and
+  ``r_i ~ U[-0.5, 0.5]^3`` (Section 5.1).
+* Ground state: the lowest ``ns`` eigenpairs of ``H = -1/2 Lap_h + V_loc + V_nl`` where
+  ``Lap_h`` is the central finite-difference Laplacian of radius ``fd_radius``.  Orbitals are
+  normalised as ``dV * sum psi^2 = 1``.  A system is re-seeded until the gap
+  ``eps_{ns+1} - eps_ns`` reaches ``min_gap`` so that the occupied set is well defined.
+
+The finite-difference weights used for the eigenproblem come from an exact rational solve
+of the moment (Vandermonde) conditions, independent of how the oracle or the CUDA library
+obtain theirs.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+from dataclasses import dataclass, field
+from fractions import Fraction
+
+import numpy as np
+
+PERIODIC, DIRICHLET = 0, 1
+_CACHE_VERSION = 3
+
+
+# ----------------------------------------------------------------------------------------
+# finite-difference weights (exact rational moment solve)
+# ----------------------------------------------------------------------------------------
+def second_derivative_weights(radius: int) -> np.ndarray:
+    """Central weights w_0..w_R with sum_j w_|j| j^k = 2*[k == 2] for even k <= 2R."""
+    R = radius
+    rows = []
+    rhs = []
+    for k in range(0, 2 * R + 1, 2):
+        row = [Fraction(1) if k == 0 else Fraction(0)]
+        row += [Fraction(2 * m ** k) for m in range(1, R + 1)]
+        rows.append(row)
+        rhs.append(Fraction(2) if k == 2 else Fraction(0))
+    n = R + 1
+    a = [r[:] + [b] for r, b in zip(rows, rhs)]
+    for c in range(n):
+        p = next(i for i in range(c, n) if a[i][c] != 0)
+        a[c], a[p] = a[p], a[c]
+        piv = a[c][c]
+        a[c] = [v / piv for v in a[c]]
+        for i in range(n):
+            if i != c and a[i][c] != 0:
+                f = a[i][c]
+                a[i] = [vi - f * vc for vi, vc in zip(a[i], a[c])]
+    return np.array([float(a[i][n]) for i in range(n)])
+
+
+def _lap1d_dense(n: int, h: float, bc: int, radius: int) -> np.ndarray:
+    w = second_derivative_weights(radius)
+    L = np.zeros((n, n))
+    for i in range(n):
+        L[i, i] += w[0]
+        for m in range(1, radius + 1):
+            for j in (i + m, i - m):
+                if bc == PERIODIC:
+                    L[i, j % n] += w[m]
+                elif 0 <= j < n:
+                    L[i, j] += w[m]
+    return L / (h * h)
+
+
+def _lap1d_symbol(n: int, h: float, radius: int) -> np.ndarray:
+    w = second_derivative_weights(radius)
+    k = np.arange(n)
+    s = np.full(n, w[0])
+    for m in range(1, radius + 1):
+        s = s + 2.0 * w[m] * np.cos(2.0 * np.pi * k * m / n)
+    return s / (h * h)
+
+
+# ----------------------------------------------------------------------------------------
+# containers
+# ----------------------------------------------------------------------------------------
+@dataclass
+class ProjectorGroup:
+    """Projectors sharing one support: ``idx`` (nnz grid indices), ``chi`` (nproj x nnz)."""
+    idx: np.ndarray
+    chi: np.ndarray
+    gamma: np.ndarray
+
+
+@dataclass
+class System:
+    name: str
+    n: tuple
+    h: tuple
+    bc: tuple
+    fd_radius: int
+    vloc: np.ndarray
+    groups: list
+    natom: int
+    ns: int
+    psi: np.ndarray = None      # (ns, N_d), dV * sum psi^2 = 1
+    eps: np.ndarray = None      # (ns,)
+    gap: float = float("nan")
+    resid: float = float("nan")
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def N_d(self) -> int:
+        return int(self.n[0] * self.n[1] * self.n[2])
+
+    @property
+    def dV(self) -> float:
+        return float(self.h[0] * self.h[1] * self.h[2])
+
+    # -- the Hamiltonian of the generator (used only to find the ground state) -----------
+    def dense_h(self) -> np.ndarray:
+        nx, ny, nz = self.n
+        Lx = _lap1d_dense(nx, self.h[0], self.bc[0], self.fd_radius)
+        Ly = _lap1d_dense(ny, self.h[1], self.bc[1], self.fd_radius)
+        Lz = _lap1d_dense(nz, self.h[2], self.bc[2], self.fd_radius)
+        Ix, Iy, Iz = np.eye(nx), np.eye(ny), np.eye(nz)
+        lap = (np.kron(Iz, np.kron(Iy, Lx)) + np.kron(Iz, np.kron(Ly, Ix))
+               + np.kron(Lz, np.kron(Iy, Ix)))
+        H = -0.5 * lap + np.diag(self.vloc)
+        for g in self.groups:
+            P = np.zeros((self.N_d, g.chi.shape[0]))
+            P[g.idx, :] = g.chi.T
+            H += self.dV * (P * g.gamma[None, :]) @ P.T
+        return H
+
+
+# ----------------------------------------------------------------------------------------
+# geometry helpers
+# ----------------------------------------------------------------------------------------
+def _axis_coords(n, L, bc):
+    if bc == PERIODIC:
+        h = L / n
+        return h, np.arange(n) * h
+    h = L / (n + 1)
+    return h, (np.arange(n) + 1) * h
+
+
+def _grid(n, L, bc):
+    hx, xs = _axis_coords(n[0], L[0], bc[0])
+    hy, ys = _axis_coords(n[1], L[1], bc[1])
+    hz, zs = _axis_coords(n[2], L[2], bc[2])
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    return (hx, hy, hz), X.ravel(), Y.ravel(), Z.ravel()
+
+
+def _disp(a, b, L, periodic):
+    d = a - b
+    if periodic:
+        d = d - L * np.round(d / L)
+    return d
+
+
+def _gauss_wells(X, Y, Z, L, bc, centres, depth, sigma):
+    v = np.zeros_like(X)
+    rng = [(-1, 0, 1) if b == PERIODIC else (0,) for b in bc]
+    for c, D, s in zip(centres, depth, sigma):
+        for ix in rng[0]:
+            for iy in rng[1]:
+                for iz in rng[2]:
+                    dx = X - (c[0] + ix * L[0])
+                    dy = Y - (c[1] + iy * L[1])
+                    dz = Z - (c[2] + iz * L[2])
+                    v -= D * np.exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * s * s))
+    return v
+
+
+def _sp_projectors(X, Y, Z, L, bc, centres, sp, gamma_rng, rng, dV, kinds=4):
+    """s/p Gaussian projectors per centre; ``gamma_rng`` = ((s_lo, s_hi), (p_lo, p_hi))."""
+    groups = []
+    rc = 3.5 * sp
+    for c in centres:
+        dx = _disp(X, c[0], L[0], bc[0] == PERIODIC)
+        dy = _disp(Y, c[1], L[1], bc[1] == PERIODIC)
+        dz = _disp(Z, c[2], L[2], bc[2] == PERIODIC)
+        r2 = dx * dx + dy * dy + dz * dz
+        idx = np.nonzero(r2 <= rc * rc)[0].astype(np.int32)
+        g = np.exp(-r2[idx] / (2.0 * sp * sp))
+        funcs = [g, dx[idx] * g, dy[idx] * g, dz[idx] * g][:kinds]
+        chi = np.stack(funcs)
+        chi /= np.sqrt(dV * np.sum(chi * chi, axis=1, keepdims=True))
+        gam = np.concatenate([rng.uniform(gamma_rng[0][0], gamma_rng[0][1], size=1),
+                              rng.uniform(gamma_rng[1][0], gamma_rng[1][1], size=kinds - 1)])
+        groups.append(ProjectorGroup(idx=idx, chi=chi, gamma=gam))
+    return groups
+
+
+def diamond_sites(a: float, ncell=(1, 1, 1)) -> np.ndarray:
+    fcc = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
+    basis = np.concatenate([fcc, fcc + 0.25])
+    out = []
+    for i in range(ncell[0]):
+        for j in range(ncell[1]):
+            for k in range(ncell[2]):
+                out.append((basis + np.array([i, j, k])) * a)
+    return np.concatenate(out)
+
+
+# ----------------------------------------------------------------------------------------
+# ground state
+# ----------------------------------------------------------------------------------------
+class _PeriodicH:
+    """H applied to blocks (m, N_d) with the kinetic term diagonal in the discrete Fourier basis."""
+
+    def __init__(self, s: System):
+        nx, ny, nz = s.n
+        kx = _lap1d_symbol(nx, s.h[0], s.fd_radius)[: nx // 2 + 1]
+        ky = _lap1d_symbol(ny, s.h[1], s.fd_radius)
+        kz = _lap1d_symbol(nz, s.h[2], s.fd_radius)
+        self.K = -0.5 * (kz[:, None, None] + ky[None, :, None] + kx[None, None, :])
+        self.shape = (nz, ny, nx)
+        self.v = s.vloc
+        self.groups = s.groups
+        self.dV = s.dV
+        self.kmax = float(self.K.max())
+
+    def __call__(self, X):
+        import scipy.fft as sfft
+        m = X.shape[0]
+        F = sfft.rfftn(X.reshape((m,) + self.shape), axes=(1, 2, 3), workers=-1)
+        F *= self.K[None]
+        Y = sfft.irfftn(F, s=self.shape, axes=(1, 2, 3), workers=-1).reshape(m, -1)
+        Y += X * self.v[None, :]
+        for g in self.groups:
+            xb = X[:, g.idx]                             # (m, nnz)
+            c = (xb @ g.chi.T) * (self.dV * g.gamma)     # (m, nproj)
+            Y[:, g.idx] += c @ g.chi
+        return Y
+
+
+def _lanczos_max(Hop, N, rng, steps=40):
+    q = rng.standard_normal(N)
+    q /= np.linalg.norm(q)
+    Q = [q]
+    al, be = [], []
+    b = 0.0
+    qprev = np.zeros(N)
+    for _ in range(steps):
+        w = Hop(q[None, :])[0]
+        a = q @ w
+        w = w - a * q - b * qprev
+        for v in Q:
+            w -= (v @ w) * v
+        b = np.linalg.norm(w)
+        al.append(a)
+        be.append(b)
+        qprev, q = q, w / b
+        Q.append(q)
+    T = np.diag(al) + np.diag(be[:-1], 1) + np.diag(be[:-1], -1)
+    th = np.linalg.eigvalsh(T)
+    return float(th[-1] + abs(be[-1]))
+
+
+def _chfsi(s: System, m: int, tol: float, seed: int, degree=24, maxit=200, log=None):
+    """Chebyshev-filtered subspace iteration for the lowest m eigenpairs (l2 normalised)."""
+    Hop = _PeriodicH(s)
+    N = s.N_d
+    rng = np.random.default_rng(seed)
+    bmax = _lanczos_max(Hop, N, rng)
+    X = rng.standard_normal((m, N))
+    X, _ = np.linalg.qr(X.T)
+    X = X.T
+    HX = Hop(X)
+    th, W = np.linalg.eigh(X @ HX.T)
+    X = W.T @ X
+    HX = W.T @ HX
+    a = float(th[-1])
+    a0 = float(th[0])
+    res = np.inf
+    for it in range(maxit):
+        # Chebyshev polynomial of (H - c)/e, normalised to 1 at a0 (damps [a, bmax]).
+        c = 0.5 * (bmax + a)
+        e = 0.5 * (bmax - a)
+        t0 = (a0 - c) / e
+        rho_prev, rho = 1.0, t0
+        Yp = X
+        Y = (HX - c * X) / e / rho
+        for _ in range(2, degree + 1):
+            rho_next = 2.0 * t0 * rho - rho_prev
+            Yn = (2.0 * (Hop(Y) - c * Y) / e * rho - rho_prev * Yp) / rho_next
+            Yp, Y = Y, Yn
+            rho_prev, rho = rho, rho_next
+        Q, _ = np.linalg.qr(Y.T)
+        Q = Q.T
+        HQ = Hop(Q)
+        S = Q @ HQ.T
+        th, W = np.linalg.eigh(0.5 * (S + S.T))
+        X = W.T @ Q
+        HX = W.T @ HQ
+        R = HX - th[:, None] * X
+        rn = np.linalg.norm(R, axis=1)
+        res = float(rn[: s.ns].max())
+        if log:
+            log(f"chfsi it {it} res {res:.3e} ritz[ns-1..ns] {th[s.ns - 1]:.6f} {th[s.ns]:.6f}")
+        if res <= tol:
+            break
+        a = float(th[-1])
+        a0 = float(th[0])
+    return th, X, res
+
+
+def _solve_ground_state(s: System, tol=1e-10, seed=0, log=None):
+    ns = s.ns
+    if s.N_d <= 4200:
+        H = s.dense_h()
+        th, V = np.linalg.eigh(H)
+        X = V[:, : ns + 1].T
+        R = H @ X.T - X.T * th[None, : ns + 1]
+        res = float(np.linalg.norm(R[:, :ns], axis=0).max())
+    else:
+        if any(b != PERIODIC for b in s.bc):
+            return _solve_ground_state_sparse(s, tol, seed)
+        m = ns + max(8, ns // 4)
+        th, X, res = _chfsi(s, m, tol, seed, log=log)
+    eps = th[: ns + 1]
+    psi = X[:ns] / np.sqrt(s.dV)
+    # deterministic sign: largest-magnitude entry positive
+    for i in range(ns):
+        j = int(np.argmax(np.abs(psi[i])))
+        if psi[i, j] < 0:
+            psi[i] = -psi[i]
+    return psi, eps[:ns].copy(), float(eps[ns] - eps[ns - 1]), res
+
+
+def _solve_ground_state_sparse(s: System, tol, seed):
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    nx, ny, nz = s.n
+    L = []
+    for ax, nn in enumerate((nx, ny, nz)):
+        L.append(sp.csr_matrix(_lap1d_dense(nn, s.h[ax], s.bc[ax], s.fd_radius)))
+    Ix, Iy, Iz = sp.identity(nx), sp.identity(ny), sp.identity(nz)
+    lap = (sp.kron(Iz, sp.kron(Iy, L[0])) + sp.kron(Iz, sp.kron(L[1], Ix))
+           + sp.kron(L[2], sp.kron(Iy, Ix)))
+    H = (-0.5 * lap + sp.diags(s.vloc)).tocsr()
+    for g in s.groups:
+        P = sp.csr_matrix((g.chi.T.ravel(), (np.repeat(g.idx, g.chi.shape[0]),
+                                             np.tile(np.arange(g.chi.shape[0]), len(g.idx)))),
+                          shape=(s.N_d, g.chi.shape[0]))
+        H = H + s.dV * (P @ sp.diags(g.gamma) @ P.T)
+    rng = np.random.default_rng(seed)
+    v0 = rng.standard_normal(s.N_d)
+    k = s.ns + 4
+    th, V = spla.eigsh(H, k=k, which="SA", tol=1e-13, v0=v0, maxiter=20000)
+    o = np.argsort(th)
+    th, V = th[o], V[:, o]
+    R = H @ V[:, : s.ns] - V[:, : s.ns] * th[None, : s.ns]
+    res = float(np.linalg.norm(R, axis=0).max())
+    return th, V.T, res
+
+
+# ----------------------------------------------------------------------------------------
+# recipes
+# ----------------------------------------------------------------------------------------
+def _cache_dir():
+    d = os.environ.get("RPA_CACHE_DIR") or os.path.join(
+        os.path.dirname(os.path.dirname(os.path.abspath(__file__))), ".cache")
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
+def gaussian_system(name, n, L, bc, centres, depth, sigma, ns, fd_radius=6,
+                    proj_sigma=None, gamma_rng=((1.5, 2.5), (-3.5, -2.5)), proj_kinds=4, seed=0,
+                    min_gap=0.05, reseed_limit=20, tol=1e-10, cache=True, log=None,
+                    _positions_fn=None):
+    """Build a system from Gaussian wells (and optional s/p projectors), then its ground state.
+
+    ``_positions_fn(rng)`` (optional) returns (centres, depth, sigma) from a generator so that
+    re-seeding for the gap moves the atoms too.
+    """
+    key = json.dumps(dict(v=_CACHE_VERSION, name=name, n=list(n), L=list(map(float, L)),
+                          bc=list(bc), ns=ns, r=fd_radius, ps=proj_sigma, g=str(gamma_rng),
+                          pk=proj_kinds, seed=seed, mg=min_gap, tol=tol,
+                          c=None if _positions_fn else np.asarray(centres).round(12).tolist(),
+                          d=None if _positions_fn else np.asarray(depth).round(12).tolist(),
+                          s=None if _positions_fn else np.asarray(sigma).round(12).tolist()),
+                     sort_keys=True)
+    digest = hashlib.sha256(key.encode()).hexdigest()[:16]
+    path = os.path.join(_cache_dir(), f"{name}_{digest}.npz")
+    if cache and os.path.exists(path):
+        return _load(path)
+    for attempt in range(reseed_limit):
+        sd = seed + 1000 * attempt
+        rng = np.random.default_rng(sd)
+        if _positions_fn is not None:
+            centres, depth, sigma = _positions_fn(rng)
+        h, X, Y, Z = _grid(n, L, bc)
+        dV = h[0] * h[1] * h[2]
+        v = _gauss_wells(X, Y, Z, L, bc, centres, depth, sigma)
+        groups = []
+        if proj_sigma is not None:
+            groups = _sp_projectors(X, Y, Z, L, bc, centres, proj_sigma, gamma_rng, rng, dV,
+                                    kinds=proj_kinds)
+        s = System(name=name, n=tuple(n), h=h, bc=tuple(bc), fd_radius=fd_radius, vloc=v,
+                   groups=groups, natom=len(centres), ns=ns)
+        psi, eps, gap, res = _solve_ground_state(s, tol=tol, seed=sd, log=log)
+        s.psi, s.eps, s.gap, s.resid = psi, eps, gap, res
+        s.meta = dict(seed=sd, attempt=attempt, L=list(map(float, L)),
+                      centres=np.asarray(centres).tolist())
+        if gap >= min_gap:
+            break
+        if log:
+            log(f"{name}: gap {gap:.4f} < {min_gap}, re-seeding")
+    if cache:
+        _save(path, s)
+    return s
+
+
+def _save(path, s: System):
+    arrs = dict(vloc=s.vloc, psi=s.psi, eps=s.eps)
+    for i, g in enumerate(s.groups):
+        arrs[f"g{i}_idx"] = g.idx
+        arrs[f"g{i}_chi"] = g.chi
+        arrs[f"g{i}_gamma"] = g.gamma
+    hdr = dict(name=s.name, n=list(s.n), h=list(s.h), bc=list(s.bc), r=s.fd_radius,
+               natom=s.natom, ns=s.ns, gap=s.gap, resid=s.resid, ngroups=len(s.groups),
+               meta=s.meta)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, header=np.frombuffer(json.dumps(hdr).encode(), dtype=np.uint8), **arrs)
+    os.replace(tmp, path)
+
+
+def _load(path) -> System:
+    z = np.load(path)
+    hdr = json.loads(bytes(z["header"]).decode())
+    groups = [ProjectorGroup(idx=z[f"g{i}_idx"], chi=z[f"g{i}_chi"], gamma=z[f"g{i}_gamma"])
+              for i in range(hdr["ngroups"])]
+    return System(name=hdr["name"], n=tuple(hdr["n"]), h=tuple(hdr["h"]), bc=tuple(hdr["bc"]),
+                  fd_radius=hdr["r"], vloc=z["vloc"], groups=groups, natom=hdr["natom"],
+                  ns=hdr["ns"], psi=z["psi"], eps=z["eps"], gap=hdr["gap"],
+                  resid=hdr["resid"], meta=hdr["meta"])
+
+
+def toy_system(seed=0, n=12, L=6.0, ns=8, fd_radius=6, nwell=4, **kw):
+    """Periodic cube with ``nwell`` Gaussian wells, no projectors (dense eigensolve)."""
+    def pos(rng):
+        c = rng.uniform(0.0, L, size=(nwell, 3))
+        d = rng.uniform(0.5, 2.0, size=nwell)
+        s = rng.uniform(0.8, 1.5, size=nwell)
+        return c, d, s
+    return gaussian_system(f"toy{n}", (n, n, n), (L, L, L), (PERIODIC,) * 3, None, None, None,
+                           ns, fd_radius=fd_radius, seed=seed, _positions_fn=pos, **kw)
+
+
+def si_like_system(ncell=(1, 1, 1), a=10.26, pts_per_cell=26, ns=None, seed=1,
+                   depth=(1.2, 1.8), sigma=1.0, proj_sigma=1.1,
+                   gamma_rng=((1.5, 2.5), (-3.5, -2.5)),
+                   fd_radius=6, **kw):
+    """Perturbed diamond-Si-like cell: Gaussian wells plus 4 s/p projectors per atom."""
+    n = tuple(pts_per_cell * c for c in ncell)
+    L = tuple(a * c for c in ncell)
+    base = diamond_sites(a, ncell)
+    nat = len(base)
+    if ns is None:
+        ns = 2 * nat
+    nn = a * np.sqrt(3.0) / 4.0
+    delta = 0.1 * nn
+
+    def pos(rng):
+        c = base + delta * rng.uniform(-0.5, 0.5, size=base.shape)
+        d = rng.uniform(depth[0], depth[1], size=nat)
+        s = np.full(nat, sigma)
+        return c, d, s
+    name = f"si{nat}_{'x'.join(map(str, n))}"
+    return gaussian_system(name, n, L, (PERIODIC,) * 3, None, None, None, ns,
+                           fd_radius=fd_radius, proj_sigma=proj_sigma, gamma_rng=gamma_rng,
+                           seed=seed, _positions_fn=pos, **kw)
+
+
+def cluster_system(natom=12, box=16.0, n=40, ns=24, seed=6, fd_radius=6, **kw):
+    """Isolated Gaussian-well cluster with zero Dirichlet walls on all axes."""
+    def pos(rng):
+        c = box / 2 + rng.uniform(-3.0, 3.0, size=(natom, 3))
+        d = rng.uniform(1.2, 1.8, size=natom)
+        s = np.full(natom, 1.0)
+        return c, d, s
+    return gaussian_system(f"cluster{natom}_{n}", (n, n, n), (box, box, box), (DIRICHLET,) * 3,
+                           None, None, None, ns, fd_radius=fd_radius, proj_sigma=1.1,
+                           seed=seed, _positions_fn=pos, **kw)
+
+
+def named_system(name: str, **kw) -> System:
+    """The workloads by name: toy (12^3), si8 (26^3), si64 (52^3)."""
+    if name == "toy":
+        return toy_system(**kw)
+    if name == "si8":
+        return si_like_system((1, 1, 1), seed=1, **kw)
+    if name == "si64":
+        return si_like_system((2, 2, 2), seed=2, **kw)
+    raise KeyError(name)
+
+
+def probe_sample(nprobe_total: int, nw: int, count: int, seed: int):
+    """Seeded sample of ``count`` (probe, frequency) pairs spread evenly over frequencies."""
+    rng = np.random.default_rng(seed)
+    per = max(1, count // nw)
+    out = []
+    for k in range(nw):
+        ps = rng.choice(nprobe_total, size=min(per, nprobe_total), replace=False)
+        out += [(int(p), k) for p in np.sort(ps)]
+    return out[:count] if count >= nw else out

@@ -1,0 +1,327 @@
+"""Pins of the CPU oracle against things other than itself (closed forms, invariants, exact
+dense targets, library routines, printed values).  No GPU needed."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+import synth
+from synth import PERIODIC, DIRICHLET
+from tests.systems_small import tiny
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- finite differences ----
+@pytest.mark.parametrize("R", [1, 2, 3, 4, 6])
+def test_fd_weights_exact_on_polynomials(R):
+    w = oracle.fd_weights(R)
+    j = np.arange(-R, R + 1)
+    wj = w[np.abs(j)]
+    for k in range(0, 2 * R + 2):
+        # second derivative of x^k at 0 is 2 for k == 2 and 0 otherwise
+        assert abs(np.sum(wj * j.astype(float) ** k) - (2.0 if k == 2 else 0.0)) < 1e-9 * (R ** k + 1)
+    # the moment conditions fix the weights uniquely: compare with the exact rational solve
+    assert np.allclose(w, synth.systems.second_derivative_weights(R), rtol=1e-13, atol=1e-15)
+    if R == 1:
+        assert np.allclose(w, [-2.0, 1.0])
+
+
+@pytest.mark.parametrize("bc", [(PERIODIC,) * 3, (DIRICHLET,) * 3, (PERIODIC, DIRICHLET, PERIODIC)])
+def test_apply_h_matches_dense_matrix(bc):
+    s = tiny(bc=bc)
+    H = s.dense_h()  # generator's own construction (Kronecker sums + explicit projectors)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((2, s.N_d)) + 1j * rng.standard_normal((2, s.N_d))
+    sig = -0.3 + 0.7j
+    y = oracle.apply_h(s, x, sig)
+    ref = (H @ x.T).T - sig * x
+    assert np.max(np.abs(y - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def test_fd_periodic_eigenvalues_equal_symbol():
+    s = tiny(n=(9, 8, 7), radius=3)
+    w = oracle.fd_weights(3)
+    for ax in range(3):
+        lam, V = oracle.nu_modes(s, ax)
+        n, h = s.n[ax], s.h[ax]
+        k = np.arange(n)
+        sym = (w[0] + 2 * sum(w[m] * np.cos(2 * np.pi * k * m / n) for m in range(1, 4))) / h ** 2
+        assert np.allclose(np.sort(lam), np.sort(sym), atol=1e-10 * np.abs(sym).max())
+        assert np.allclose(V.T @ V, np.eye(n), atol=1e-12)
+
+
+# ---------------------------------------------------------------- Coulomb square root ----
+def _fft_poisson(s, x):
+    """nu x = -4 pi Lap_h^+ x for a periodic cell, from the FD symbol in Fourier space."""
+    w = oracle.fd_weights(s.fd_radius)
+    syms = []
+    for ax in range(3):
+        n, h = s.n[ax], s.h[ax]
+        k = np.arange(n)
+        syms.append((w[0] + 2 * sum(w[m] * np.cos(2 * np.pi * k * m / n)
+                                    for m in range(1, s.fd_radius + 1))) / h ** 2)
+    lam = syms[2][:, None, None] + syms[1][None, :, None] + syms[0][None, None, :]
+    X = np.fft.fftn(x.reshape(s.n[2], s.n[1], s.n[0]))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        mult = np.where(np.abs(lam) > 1e-9, -4 * np.pi / lam, 0.0)
+    return np.real(np.fft.ifftn(X * mult)).ravel()
+
+
+def test_nu_half_squares_to_fft_poisson():
+    s = tiny(n=(8, 6, 7), radius=3)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(s.N_d)
+    u = oracle.nu_half(s, oracle.nu_half(s, x)[0])[0]
+    ref = _fft_poisson(s, x)
+    assert np.max(np.abs(u - ref)) < 1e-11 * np.max(np.abs(ref))
+    # nu^{1/2} annihilates the constant vector (periodic zero mode)
+    assert np.max(np.abs(oracle.nu_half(s, np.ones(s.N_d))[0])) < 1e-11
+
+
+@pytest.mark.parametrize("bc", [(DIRICHLET,) * 3, (PERIODIC, DIRICHLET, DIRICHLET)])
+def test_nu_half_inverts_laplacian(bc):
+    s = tiny(bc=bc, radius=2)
+    lap = dense.dense_laplacian(s.n, s.h, s.bc, synth.systems.second_derivative_weights(2))
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal(s.N_d)
+    if PERIODIC in bc:
+        # remove the null-space component of lap (constant along every periodic axis)
+        lam, U = np.linalg.eigh(lap)
+        null = U[:, np.abs(lam) < 1e-9 * np.abs(lam).max()]
+        x = x - null @ (null.T @ x)
+    nx = oracle.nu_half(s, oracle.nu_half(s, x)[0])[0]
+    # -lap (nu x) = 4 pi x on the range
+    assert np.max(np.abs(-lap @ nx - 4 * np.pi * x)) < 1e-9 * 4 * np.pi * np.abs(x).max()
+    # and nu^{1/2} equals the dense symmetric square root
+    S = dense.nu_half_dense(lap)
+    assert np.max(np.abs(oracle.nu_half(s, x)[0] - S @ x)) < 1e-10 * np.abs(S @ x).max()
+
+
+# ---------------------------------------------------------------- frequencies ----------
+def test_gl_frequencies_match_printed_table():
+    printed = np.loadtxt(os.path.join(GOLD, "gl_omega_table3.txt"))
+    om, w = oracle.gl_frequencies(8)
+    # Printed to two decimals; the largest node is 49.36497, printed 49.37 (a rounding through
+    # 49.365), so allow half a unit of the last digit plus that double rounding.
+    assert np.all(np.abs(om - printed) <= 0.0051)
+    assert np.sum(np.round(om, 2) == printed) == 7
+    assert abs(np.sum(w / (1 + om ** 2)) - np.pi / 2) < 1e-5
+
+
+@pytest.mark.parametrize("nw", [1, 2, 5, 8, 10, 16])
+def test_gl_underlying_rule_is_exact_for_polynomials(nw):
+    om, W = oracle.gl_frequencies(nw)
+    x = (om - 1) / (om + 1)               # invert omega = (1+x)/(1-x)
+    w = W * (1 - x) ** 2 / 2              # invert the Jacobian
+    for k in range(2 * nw):
+        exact = (1 - (-1) ** (k + 1)) / (k + 1)
+        assert abs(np.sum(w * x ** k) - exact) < 1e-12
+    # a rational integrand that the mapped rule converges on: int_0^inf dw/(1+w^2) = pi/2
+    if nw >= 16:
+        assert abs(np.sum(W / (1 + om ** 2)) - np.pi / 2) < 1e-10
+
+
+# ---------------------------------------------------------------- response function -----
+@pytest.mark.parametrize("bc", [(PERIODIC,) * 3, (DIRICHLET,) * 3])
+@pytest.mark.parametrize("omega", [0.02, 0.69, 8.84])
+def test_chi0_sternheimer_equals_sum_over_states(bc, omega):
+    s = tiny(bc=bc)
+    H = s.dense_h()
+    K, _ = dense.chi0_dense(H, s.ns, s.dV, omega)
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(s.N_d)
+    r, it = oracle.chi0(s, omega, u, tol=1e-13)
+    ref = K @ u
+    assert np.max(np.abs(r - ref)) < 1e-9 * np.max(np.abs(ref))
+    # symmetric and negative semidefinite
+    v = rng.standard_normal(s.N_d)
+    rv, _ = oracle.chi0(s, omega, v, tol=1e-13)
+    assert abs(v @ r - u @ rv) < 1e-9 * abs(u @ r)
+    assert u @ r < 0 and v @ rv < 0
+
+
+def test_chi0_iterations_grow_as_omega_decreases():
+    s = tiny()
+    u = np.random.default_rng(4).standard_normal(s.N_d)
+    its = [oracle.chi0(s, om, u, tol=1e-8)[1].sum() for om in (49.37, 3.22, 0.31, 0.02)]
+    assert its[0] <= its[1] <= its[2] <= its[3]
+
+
+# ---------------------------------------------------------------- Lanczos quadrature ----
+@pytest.fixture(scope="module")
+def tiny_exact():
+    s = tiny()
+    H = s.dense_h()
+    lap = dense.dense_laplacian(s.n, s.h, s.bc, synth.systems.second_derivative_weights(s.fd_radius))
+    omega = 0.31
+    out = {}
+    for fk in (0, 1, 2):
+        out[fk] = dense.exact_diagonal(H, lap, s.ns, s.dV, omega, fkind=fk)
+    return s, omega, out
+
+
+def test_spectrum_nonpositive(tiny_exact):
+    s, omega, out = tiny_exact
+    lam = out[0][2]
+    assert lam.max() < 1e-10 and lam.min() < 0
+
+
+def test_gauss_quadrature_exactness(tiny_exact):
+    s, omega, out = tiny_exact
+    A = out[0][3]
+    probes = np.array([0, 17, 100, s.N_d - 1])
+    # one step integrates f(x) = x exactly: d = A_jj
+    r1 = oracle.lanczos(s, probes, omega, nl=1, tol=1e-13, fkind=oracle.F_X)
+    assert np.allclose(r1["d"], np.diag(A)[probes], rtol=1e-9, atol=1e-13)
+    # two steps integrate f(x) = x^2 exactly: d = (A^2)_jj = ||A e_j||^2
+    r2 = oracle.lanczos(s, probes, omega, nl=2, tol=1e-13, fkind=oracle.F_X2)
+    assert np.allclose(r2["d"], np.sum(A[:, probes] ** 2, axis=0), rtol=1e-9, atol=1e-13)
+
+
+def test_quadrature_monotone_one_sided_bound(tiny_exact):
+    """f has negative even derivatives, so Gauss estimates decrease monotonically to the
+    exact value from above: 0 >= d^(1) >= d^(2) >= ... >= [f(A)]_jj."""
+    s, omega, out = tiny_exact
+    dex = out[0][0]
+    probes = np.array([5, 60, 200])
+    prev = np.zeros(len(probes))
+    for k in range(1, 7):
+        d = oracle.lanczos(s, probes, omega, nl=k, tol=1e-13)["d"]
+        assert np.all(d <= prev + 1e-12)
+        assert np.all(d >= dex[probes] - 1e-12)
+        prev = d
+
+
+def test_lanczos_converges_to_exact_diagonal(tiny_exact):
+    s, omega, out = tiny_exact
+    dex = out[0][0]
+    probes = np.arange(0, s.N_d, 37)
+    d = oracle.lanczos(s, probes, omega, nl=30, tol=1e-13)["d"]
+    assert np.max(np.abs(d - dex[probes])) < 1e-9 * np.max(np.abs(dex))
+
+
+def test_tridiag_f11_against_library_eigensolver():
+    import scipy.linalg as sla
+    rng = np.random.default_rng(5)
+    for k in (1, 2, 5, 17, 40):
+        al = -rng.uniform(0.01, 2.0, size=k)
+        be = rng.uniform(0.01, 0.5, size=max(k - 1, 0))
+        if k > 1:
+            lam, Q = sla.eigh_tridiagonal(al, be)
+        else:
+            lam, Q = al.copy(), np.ones((1, 1))
+        assert lam.max() < 1.0
+        ref = np.sum(Q[0] ** 2 * (np.log1p(-lam) + lam))
+        assert abs(oracle.tridiag_f11(al, be) - ref) < 1e-12 * max(1.0, abs(ref))
+        # f(x) = x and x^2 have closed forms: alpha_1 and alpha_1^2 + beta_1^2
+        assert abs(oracle.tridiag_f11(al, be, oracle.F_X) - al[0]) < 1e-12
+        b1 = be[0] if k > 1 else 0.0
+        assert abs(oracle.tridiag_f11(al, be, oracle.F_X2) - (al[0] ** 2 + b1 ** 2)) < 1e-12
+
+
+def test_trace_and_energy_sign():
+    """At g = 1 and converged quadrature, sum_j d_j = Tr f(A), and E_c < 0."""
+    s = tiny(n=(5, 6, 5), ns=2)
+    H = s.dense_h()
+    lap = dense.dense_laplacian(s.n, s.h, s.bc, synth.systems.second_derivative_weights(s.fd_radius))
+    om, w = oracle.gl_frequencies(3)
+    res = oracle.energy(s, om, w, stride=(1, 1, 1), nl=25, tol=1e-12)
+    ec_ref = 0.0
+    for k in range(3):
+        d, tr, lam, *_ = dense.exact_diagonal(H, lap, s.ns, s.dV, om[k])
+        assert abs(res["d_fine"][k].sum() - tr) < 1e-8 * abs(tr)
+        ec_ref += w[k] * tr
+    ec_ref /= 2 * np.pi
+    assert res["ec"] < 0
+    assert abs(res["ec"] - ec_ref) < 1e-8 * abs(ec_ref)
+
+
+def test_h_refinement_normalisation():
+    """The same physical cell at three spacings: the integrand Tr f(A) converges instead of
+    scaling with the volume element (a missing or doubled dV fails this)."""
+    vals = []
+    for n in (6, 8, 10):
+        L = 4.0
+        s = synth.gaussian_system(f"href{n}", (n, n, n), (L, L, L), (PERIODIC,) * 3,
+                                  [[2.0, 2.0, 2.0]], [1.5], [0.9], 1, fd_radius=3,
+                                  min_gap=0.0, cache=False)
+        H = s.dense_h()
+        lap = dense.dense_laplacian(s.n, s.h, s.bc, synth.systems.second_derivative_weights(3))
+        vals.append(dense.exact_diagonal(H, lap, 1, s.dV, 0.5)[1])
+        # oracle chi0 normalisation agrees with the dense one at every spacing
+        u = np.random.default_rng(n).standard_normal(s.N_d)
+        K, _ = dense.chi0_dense(H, 1, s.dV, 0.5)
+        assert np.allclose(oracle.chi0(s, 0.5, u, tol=1e-13)[0], K @ u, rtol=1e-8, atol=1e-12)
+    d1, d2 = abs(vals[1] - vals[0]), abs(vals[2] - vals[1])
+    assert d2 < d1
+    assert d1 < 0.2 * abs(vals[0])           # a dV error would change it by (h ratio)^3 ~ 2.4x
+
+
+# ---------------------------------------------------------------- interpolation --------
+def _poly(shape, coef_deg):
+    z, y, x = np.meshgrid(*(np.arange(n, dtype=float) for n in shape[::-1]), indexing="ij")
+    dx, dy, dz = coef_deg
+    return (1 + 0.3 * x ** dx - 0.1 * x) * (2 - 0.05 * y ** dy + 0.2 * y) * (0.5 + 0.01 * z ** dz)
+
+
+@pytest.mark.parametrize("kind,deg", [("cubic", 3), ("linear", 1)])
+def test_interpolation_exact_on_polynomials_dirichlet(kind, deg):
+    shape = (13, 10, 11)
+    bc = (DIRICHLET,) * 3
+    stride = (2, 3, 2)
+    f = _poly(shape, (deg, deg, deg)).ravel()
+    probes = oracle.coarse_probes(shape, stride, bc)
+    fh = oracle.interpolate(f[probes], shape, stride, bc, kind)
+    assert np.max(np.abs(fh - f)) < 1e-10 * np.abs(f).max()
+
+
+def test_interpolation_identity_at_coarse_points_and_g1():
+    shape = (12, 12, 12)
+    bc = (PERIODIC,) * 3
+    rng = np.random.default_rng(6)
+    for kind in ("cubic", "linear", "fourier"):
+        dc = rng.standard_normal(6 ** 3)
+        fh = oracle.interpolate(dc, shape, (2, 2, 2), bc, kind)
+        assert np.allclose(fh[oracle.coarse_probes(shape, (2, 2, 2), bc)], dc, atol=1e-12)
+    d = rng.standard_normal(12 ** 3)
+    assert np.array_equal(oracle.interpolate(d, shape, (1, 1, 1), bc, "none"), d)
+
+
+def test_interpolation_periodic_cubic_exact_away_from_wrap():
+    shape = (16, 12, 14)
+    bc = (PERIODIC,) * 3
+    f = _poly(shape, (3, 3, 3)).reshape(shape[2], shape[1], shape[0])
+    probes = oracle.coarse_probes(shape, (2, 2, 2), bc)
+    fh = oracle.interpolate(f.ravel()[probes], shape, (2, 2, 2), bc, "cubic").reshape(f.shape)
+    # interior fine points whose 4-point stencil (coarse nodes c-1..c+2) does not wrap
+    sl = tuple(slice(2, n - 3) for n in (shape[2], shape[1], shape[0]))
+    assert np.max(np.abs(fh[sl] - f[sl])) < 1e-10 * np.abs(f).max()
+
+
+def test_interpolation_sum_invariance_periodic():
+    """Shift-invariant partition-of-unity interpolants give sum(fine) = g^3 sum(coarse)."""
+    shape = (12, 12, 12)
+    bc = (PERIODIC,) * 3
+    dc = np.random.default_rng(7).standard_normal(6 ** 3)
+    for kind in ("cubic", "linear", "fourier"):
+        fh = oracle.interpolate(dc, shape, (2, 2, 2), bc, kind)
+        assert abs(fh.sum() - 8 * dc.sum()) < 1e-10 * np.abs(dc).sum()
+
+
+def test_fourier_interpolation_exact_on_bandlimited():
+    shape = (12, 8, 10)
+    bc = (PERIODIC,) * 3
+    z, y, x = np.meshgrid(*(np.arange(n) for n in shape[::-1]), indexing="ij")
+    f = (1 + np.cos(2 * np.pi * x / 12) + 0.5 * np.sin(2 * np.pi * y / 8)
+         * np.cos(2 * np.pi * z / 10)).ravel()
+    probes = oracle.coarse_probes(shape, (2, 2, 2), bc)
+    fh = oracle.interpolate(f[probes], shape, (2, 2, 2), bc, "fourier")
+    assert np.max(np.abs(fh - f)) < 1e-12
+
+
+def test_error_metrics_definition():
+    m = oracle.error_metrics(np.array([1.0, 2.0, 3.0]), np.array([1.5, 1.5, 3.0]))
+    assert m["abs_err"] == 0.0 and m["l1"] == 1.0 and m["ecr"] == 0.0
