@@ -1,0 +1,1301 @@
+// C ABI and host orchestration of the GB300 RPA library.
+//
+// Work is organised in waves of B probe-points (coarse point j, frequency w).  For every
+// Lanczos step of a wave: u = nu^{1/2} q_k (mode products), Galerkin guess over the occupied
+// space, B x N_s Sternheimer solves by batched COCG, density r = 4 sum_n psi_n Re(dpsi_n),
+// v = nu^{1/2} r, then the Lanczos recurrence with full reorthogonalisation.  Probes leave the
+// wave individually (early exit, breakdown); their systems are idle from then on.  After the
+// wave, [f(T)]_{11} gives d_j (Algorithm 1).  Interpolation and the E_c sum follow per
+// frequency (Section 3.2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cocg.cuh"
+#include "small.cuh"
+
+using namespace rpa;
+
+namespace rpa {
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+DevBuf::~DevBuf() { release(); }
+cudaError_t DevBuf::ensure(size_t nbytes) {
+  if (nbytes == 0) nbytes = 16;
+  if (p && bytes >= nbytes) return cudaSuccess;
+  release();
+  cudaError_t e = cudaMalloc(&p, nbytes);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    bytes = 0;
+    return e;
+  }
+  bytes = nbytes;
+  return cudaSuccess;
+}
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+}  // namespace rpa
+
+// ---------------------------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct OpData {
+  DevBuf vloc, psi, g_chi, coef, p_chi, nuV[3], nuVt[3], nuScale;
+  Stencil<T> st;
+};
+
+struct rpa_ctx {
+  rpa_grid grid;
+  long long nd = 0;
+  double dV = 0.0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  rpa_options opt;
+  bool have_vloc = false, have_occ = false, have_freq = false;
+  int ns = 0, nw = 0;
+  std::vector<double> omega, weight;
+  DevBuf eps_d, omega_d, weight_d;
+  OpData<double> d64;
+  OpData<float> d32;
+  int ngroup = 0;
+  DevBuf g_off, g_idx, p_off, p_grp;
+  DevBuf lam[3];
+  // interpolation operators (transposed, coarse x fine) per axis
+  DevBuf interpWt[3], cnodes_d[3];
+  std::vector<long long> cnodes[3];
+  int interp_built = -1, stride_built[3] = {0, 0, 0};
+  // wave workspace
+  DevBuf Q, u64, v64, dens64, t64a, t64b, u32, t32a, t32b;
+  DevBuf x, r, p, w, x64, r64, cdot, part, sysd, sysi, gpart, cmat;
+  DevBuf probe_d, pomega_d, active_d, steps_d, alpha_d, beta_d, lstate_d, coef_d, dots_d,
+      dotpart_d, flags_d, dout_d, counts_d;
+  int ws_nb = 0;
+  int* pinned = nullptr;  // counts from the device
+  std::string err;
+  cudaEvent_t ev[8];
+  bool have_events = false;
+};
+
+namespace rpa {
+rpa_status fail(rpa_ctx* c, rpa_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+rpa_status cuda_fail(rpa_ctx* c, cudaError_t e, const char* where) {
+  if (c) c->err = std::string("CUDA error ") + cudaGetErrorString(e) + " in " + where;
+  return RPA_ECUDA;
+}
+}  // namespace rpa
+
+#define CK(call)                                                  \
+  do {                                                            \
+    cudaError_t e__ = (call);                                     \
+    if (e__ != cudaSuccess) return rpa::cuda_fail(c, e__, #call); \
+  } while (0)
+#define CKS(call)                      \
+  do {                                 \
+    rpa_status s__ = (call);           \
+    if (s__ != RPA_OK) return s__;     \
+  } while (0)
+
+// Central second-derivative weights of radius R (order 2R):
+// c_m = (2/m^2) (-1)^{m+1} prod_{i=1}^{m} (R - i + 1)/(R + i), c_0 = -2 sum c_m.
+static void fd_weights(int R, double* c) {
+  double s = 0.0;
+  for (int m = 1; m <= R; ++m) {
+    double prod = 1.0;
+    for (int i = 1; i <= m; ++i) prod *= (double)(R - i + 1) / (double)(R + i);
+    const double v = 2.0 / ((double)m * m) * prod;
+    c[m] = (m & 1) ? v : -v;
+    s += c[m];
+  }
+  c[0] = -2.0 * s;
+}
+
+template <typename T>
+static void make_stencil(const rpa_grid& g, Stencil<T>& st) {
+  double c[kMaxRadius + 1];
+  fd_weights(g.fd_radius, c);
+  st.nx = g.n[0];
+  st.ny = g.n[1];
+  st.nz = g.n[2];
+  st.R = g.fd_radius;
+  st.bcx = g.bc[0];
+  st.bcy = g.bc[1];
+  st.bcz = g.bc[2];
+  const double ix2 = 1.0 / (g.h[0] * g.h[0]), iy2 = 1.0 / (g.h[1] * g.h[1]),
+               iz2 = 1.0 / (g.h[2] * g.h[2]);
+  for (int m = 0; m <= kMaxRadius; ++m) {
+    st.cx[m] = st.cy[m] = st.cz[m] = (T)0;
+  }
+  for (int m = 1; m <= g.fd_radius; ++m) {
+    st.cx[m] = (T)(-0.5 * c[m] * ix2);
+    st.cy[m] = (T)(-0.5 * c[m] * iy2);
+    st.cz[m] = (T)(-0.5 * c[m] * iz2);
+  }
+  st.c0 = (T)(-0.5 * c[0] * (ix2 + iy2 + iz2));
+}
+
+template <typename T>
+static OpData<T>& opd(rpa_ctx* c);
+template <>
+OpData<double>& opd<double>(rpa_ctx* c) { return c->d64; }
+template <>
+OpData<float>& opd<float>(rpa_ctx* c) { return c->d32; }
+
+template <typename T>
+static NonlocalDev<T> nlview(rpa_ctx* c) {
+  NonlocalDev<T> nl;
+  OpData<T>& o = opd<T>(c);
+  nl.ngroup = c->ngroup;
+  nl.g_off = c->g_off.as<int>();
+  nl.g_idx = c->g_idx.as<int>();
+  nl.g_chi = o.g_chi.template as<T>();
+  nl.coef = o.coef.template as<T>();
+  nl.p_off = c->p_off.as<int>();
+  nl.p_grp = c->p_grp.as<int>();
+  nl.p_chi = o.p_chi.template as<T>();
+  return nl;
+}
+
+static rpa_status copy_in(rpa_ctx* c, void* dst, const void* src, size_t bytes, int where) {
+  CK(cudaMemcpyAsync(dst, src, bytes,
+                     where == RPA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     c->stream));
+  return RPA_OK;
+}
+static rpa_status copy_out(rpa_ctx* c, void* dst, const void* src, size_t bytes, int where) {
+  CK(cudaMemcpyAsync(dst, src, bytes,
+                     where == RPA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     c->stream));
+  return RPA_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// nu^{1/2}: eigenbases of the 1-D Laplacians (device Jacobi), then u = V S V^T q
+// ---------------------------------------------------------------------------------------------
+static rpa_status build_nu(rpa_ctx* c) {
+  double cw[kMaxRadius + 1];
+  fd_weights(c->grid.fd_radius, cw);
+  double lmax = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const int n = c->grid.n[a];
+    const double h2 = c->grid.h[a] * c->grid.h[a];
+    std::vector<double> L((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+      L[(size_t)i * n + i] += cw[0] / h2;
+      for (int m = 1; m <= c->grid.fd_radius; ++m)
+        for (int sg = -1; sg <= 1; sg += 2) {
+          int j = i + sg * m;
+          if (c->grid.bc[a] == RPA_PERIODIC) {
+            j %= n;
+            if (j < 0) j += n;
+          } else if (j < 0 || j >= n) {
+            continue;
+          }
+          L[(size_t)i * n + j] += cw[m] / h2;
+        }
+    }
+    // Gershgorin bound of |lambda| for the null-space threshold
+    double rowmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double rs = 0.0;
+      for (int j = 0; j < n; ++j) rs += std::fabs(L[(size_t)i * n + j]);
+      rowmax = std::max(rowmax, rs);
+    }
+    lmax += rowmax;
+    DevBuf A;
+    CK(A.ensure(sizeof(double) * n * n));
+    CK(c->d64.nuV[a].ensure(sizeof(double) * n * n));
+    CK(c->d64.nuVt[a].ensure(sizeof(double) * n * n));
+    CK(c->d32.nuV[a].ensure(sizeof(float) * n * n));
+    CK(c->d32.nuVt[a].ensure(sizeof(float) * n * n));
+    CK(c->lam[a].ensure(sizeof(double) * n));
+    CK(cudaMemcpyAsync(A.p, L.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, c->stream));
+    CK(jacobi_eig(A.as<double>(), c->d64.nuV[a].as<double>(), c->lam[a].as<double>(), n,
+                  c->stream));
+    // transpose and FP32 copies (small: via the host)
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<double> V((size_t)n * n), Vt((size_t)n * n);
+    CK(cudaMemcpy(V.data(), c->d64.nuV[a].p, sizeof(double) * n * n, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) Vt[(size_t)j * n + i] = V[(size_t)i * n + j];
+    std::vector<float> Vf(V.begin(), V.end()), Vtf(Vt.begin(), Vt.end());
+    CK(cudaMemcpy(c->d64.nuVt[a].p, Vt.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d32.nuV[a].p, Vf.data(), sizeof(float) * n * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d32.nuVt[a].p, Vtf.data(), sizeof(float) * n * n, cudaMemcpyHostToDevice));
+  }
+  CK(c->d64.nuScale.ensure(sizeof(double) * c->nd));
+  CK(c->d32.nuScale.ensure(sizeof(float) * c->nd));
+  CK(nu_scale(c->lam[0].as<double>(), c->lam[1].as<double>(), c->lam[2].as<double>(),
+              c->grid.n[0], c->grid.n[1], c->grid.n[2], lmax, c->d64.nuScale.as<double>(),
+              c->d32.nuScale.as<float>(), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return RPA_OK;
+}
+
+// out_b = nu^{1/2} in_b for nb vectors (input batch stride in_bs, output contiguous).
+template <typename T, typename TI, typename TO>
+static rpa_status nu_half(rpa_ctx* c, const TI* in, long long in_bs, TO* out, int nb, T* ta,
+                          T* tb) {
+  OpData<T>& o = opd<T>(c);
+  const int* n = c->grid.n;
+  const long long nd = c->nd;
+  int dims[3] = {n[0], n[1], n[2]};
+  // forward: V^T along x, y, z, then the spectral scale
+  CK((mode_product<TI, T, T>(in, in_bs, ta, nd, o.nuV[0].template as<T>(), 0, dims, n[0], nb,
+                             nullptr, c->stream)));
+  CK((mode_product<T, T, T>(ta, nd, tb, nd, o.nuV[1].template as<T>(), 1, dims, n[1], nb, nullptr,
+                            c->stream)));
+  CK((mode_product<T, T, T>(tb, nd, ta, nd, o.nuV[2].template as<T>(), 2, dims, n[2], nb,
+                            o.nuScale.template as<T>(), c->stream)));
+  // inverse: V along x, y, z
+  CK((mode_product<T, T, T>(ta, nd, tb, nd, o.nuVt[0].template as<T>(), 0, dims, n[0], nb,
+                            nullptr, c->stream)));
+  CK((mode_product<T, T, T>(tb, nd, ta, nd, o.nuVt[1].template as<T>(), 1, dims, n[1], nb,
+                            nullptr, c->stream)));
+  CK((mode_product<T, TO, T>(ta, nd, out, nd, o.nuVt[2].template as<T>(), 2, dims, n[2], nb,
+                             nullptr, c->stream)));
+  return RPA_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------------------------
+static size_t cpx_bytes(const rpa_ctx* c) {
+  return c->opt.precision == RPA_FP64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
+}
+
+static long long tiles_of(long long nd) { return (nd + kTile - 1) / kTile; }
+
+static int gram_chunks(long long nd) {
+  return (int)std::max<long long>(1, std::min<long long>(256, (nd + 4095) / 4096));
+}
+
+static size_t per_probe_bytes(const rpa_ctx* c) {
+  const long long nd = c->nd, ns = c->ns;
+  size_t b = (size_t)ns * nd * cpx_bytes(c) * 4;
+  if (c->opt.precision == RPA_MIXED && c->opt.refine > 0) b += (size_t)ns * nd * 32;
+  b += (size_t)(c->opt.lanczos_max + 1) * nd * 8 + (size_t)nd * 8 * 5 + (size_t)nd * 4 * 3;
+  b += (size_t)ns * tiles_of(nd) * 4 * 8 + (size_t)ns * (kSysD * 8 + kSysI * 4);
+  b += (size_t)ns * ns * (gram_chunks(nd) * 8 + 16);
+  b += (size_t)ns * std::max(1, c->ngroup) * kProjChunk * 16;
+  return b;
+}
+
+static int choose_batch(rpa_ctx* c, long long count) {
+  int nb = c->opt.batch;
+  if (nb <= 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = (size_t)8 << 30;
+    const size_t avail = (size_t)(0.55 * (double)fr);
+    nb = (int)std::max<size_t>(1, avail / std::max<size_t>(1, per_probe_bytes(c)));
+    nb = std::min(nb, 512);
+  }
+  nb = std::min<long long>(nb, std::max<long long>(1, count));
+  nb = std::min(nb, std::max(1, 65535 / std::max(1, c->ns)));
+  return nb;
+}
+
+static rpa_status ensure_workspace(rpa_ctx* c, int nb) {
+  const long long nd = c->nd, S = (long long)nb * c->ns;
+  const int nl = c->opt.lanczos_max;
+  const size_t cb = cpx_bytes(c);
+  CK(c->Q.ensure(sizeof(double) * nb * (nl + 1) * nd));
+  CK(c->u64.ensure(sizeof(double) * nb * nd));
+  CK(c->v64.ensure(sizeof(double) * nb * nd));
+  CK(c->dens64.ensure(sizeof(double) * nb * nd));
+  CK(c->t64a.ensure(sizeof(double) * nb * nd));
+  CK(c->t64b.ensure(sizeof(double) * nb * nd));
+  if (c->opt.precision == RPA_MIXED) {
+    CK(c->u32.ensure(sizeof(float) * nb * nd));
+    CK(c->t32a.ensure(sizeof(float) * nb * nd));
+    CK(c->t32b.ensure(sizeof(float) * nb * nd));
+    if (c->opt.refine > 0) {
+      CK(c->x64.ensure(sizeof(cpx<double>) * S * nd));
+      CK(c->r64.ensure(sizeof(cpx<double>) * S * nd));
+    }
+  }
+  CK(c->x.ensure(cb * S * nd));
+  CK(c->r.ensure(cb * S * nd));
+  CK(c->p.ensure(cb * S * nd));
+  CK(c->w.ensure(cb * S * nd));
+  CK(c->cdot.ensure(sizeof(cpx<double>) * S * std::max(1, c->ngroup) * kProjChunk));
+  CK(c->part.ensure(sizeof(double) * S * tiles_of(nd) * 4));
+  CK(c->sysd.ensure(sizeof(double) * S * kSysD));
+  CK(c->sysi.ensure(sizeof(int) * S * kSysI));
+  CK(c->gpart.ensure(sizeof(double) * nb * gram_chunks(nd) * c->ns * c->ns));
+  CK(c->cmat.ensure(cb * nb * c->ns * c->ns));
+  CK(c->probe_d.ensure(sizeof(long long) * nb));
+  CK(c->pomega_d.ensure(sizeof(double) * nb));
+  CK(c->active_d.ensure(sizeof(int) * nb));
+  CK(c->steps_d.ensure(sizeof(int) * nb));
+  CK(c->alpha_d.ensure(sizeof(double) * nb * nl));
+  CK(c->beta_d.ensure(sizeof(double) * nb * nl));
+  CK(c->lstate_d.ensure(sizeof(double) * nb * 4));
+  CK(c->coef_d.ensure(sizeof(double) * nb * (nl + 2)));
+  CK(c->dots_d.ensure(sizeof(double) * nb * (nl + 2)));
+  CK(c->dotpart_d.ensure(sizeof(double) * nb * 64 * (nl + 2)));
+  CK(c->flags_d.ensure(sizeof(int) * 4));
+  CK(c->dout_d.ensure(sizeof(double) * nb));
+  CK(c->counts_d.ensure(sizeof(int) * 16));
+  c->ws_nb = nb;
+  return RPA_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// statistics
+// ---------------------------------------------------------------------------------------------
+struct SolveStats {
+  long long solves = 0, iters = 0, refine_rounds = 0;
+  int max_iters = 0, nonconv = 0, breakdown = 0;
+};
+
+static rpa_status collect_stats(rpa_ctx* c, int S, SolveStats& ss) {
+  std::vector<int> si((size_t)S * kSysI);
+  CK(cudaMemcpyAsync(si.data(), c->sysi.p, sizeof(int) * S * kSysI, cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int s = 0; s < S; ++s) {
+    const int st = si[(size_t)s * kSysI + kStatus];
+    if (st == kIdle) continue;
+    const int it = si[(size_t)s * kSysI + kIters];
+    ss.solves += 1;
+    ss.iters += it;
+    ss.max_iters = std::max(ss.max_iters, it);
+    ss.refine_rounds += si[(size_t)s * kSysI + kRestarts];
+    if (st == kMaxit) ss.nonconv += 1;
+    if (st == kBreakdown) ss.breakdown += 1;
+  }
+  return RPA_OK;
+}
+
+static rpa_status counts(rpa_ctx* c, int S, int* out) {
+  CK(count_status(S, c->sysi.as<int>(), c->counts_d.as<int>(), c->stream));
+  CK(cudaMemcpyAsync(c->pinned, c->counts_d.p, sizeof(int) * kNumStatus, cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < kNumStatus; ++i) out[i] = c->pinned[i];
+  return RPA_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Sternheimer solves for nb probe slots: dens_b = chi0(i w_b) u_b
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+static CocgView<T> make_view(rpa_ctx* c, int nb, const T* u, cpx<T>* x, cpx<T>* r, cpx<T>* p,
+                             cpx<T>* w) {
+  CocgView<T> cv;
+  OpData<T>& o = opd<T>(c);
+  cv.st = o.st;
+  cv.vloc = o.vloc.template as<T>();
+  cv.nl = nlview<T>(c);
+  cv.nd = c->nd;
+  cv.nsys = nb * c->ns;
+  cv.ns = c->ns;
+  cv.tiles = (int)tiles_of(c->nd);
+  cv.psi = o.psi.template as<T>();
+  cv.eps = c->eps_d.as<double>();
+  cv.omega = c->pomega_d.as<double>();
+  cv.u = u;
+  cv.x = x;
+  cv.r = r;
+  cv.p = p;
+  cv.w = w;
+  cv.cdot = c->cdot.as<cpx<T>>();
+  cv.part = c->part.as<double>();
+  cv.sysd = c->sysd.as<double>();
+  cv.sysi = c->sysi.as<int>();
+  return cv;
+}
+
+constexpr int kChunkIters = 4;
+
+template <typename T>
+static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv, int maxit) {
+  int cnt[kNumStatus];
+  int done_iters = 0;
+  for (;;) {
+    for (int j = 0; j < kChunkIters; ++j) CK(cocg_iteration<T>(cv, c->opt.stern_tol, maxit, c->stream));
+    done_iters += kChunkIters;
+    CKS(counts(c, cv.nsys, cnt));
+    if (cnt[kActive] == 0) break;
+    if (done_iters > maxit + 2 * kChunkIters) break;  // every system is marked by then
+  }
+  return RPA_OK;
+}
+
+// FP64 form: Galerkin guess, COCG, true-residual recheck with restart (as in the oracle).
+static rpa_status solve_fp64(rpa_ctx* c, int nb, const double* u, const int* active,
+                             SolveStats& ss) {
+  const int S = nb * c->ns;
+  const int maxit = c->opt.stern_maxit;
+  cpx<double>*x = c->x.as<cpx<double>>(), *r = c->r.as<cpx<double>>(),
+             *p = c->p.as<cpx<double>>(), *w = c->w.as<cpx<double>>();
+  CocgView<double> cv = make_view<double>(c, nb, u, x, r, p, w);
+  CK(galerkin_guess<double>(c->nd, c->ns, nb, c->d64.psi.as<double>(), c->eps_d.as<double>(),
+                            c->pomega_d.as<double>(), u, active, c->dV, c->gpart.as<double>(),
+                            gram_chunks(c->nd), c->cmat.as<cpx<double>>(), x, c->stream));
+  CK(set_status(S, c->ns, active, kActive, c->sysi.as<int>(), c->stream));
+  CK(proj_dots<double>(cv.nl, c->nd, S, x, cv.sysi, 1 << kActive, cv.cdot, c->stream));
+  CK((cocg_resid<double, double>(cv, x, r, p, 1 << kActive, nullptr, nullptr, nullptr,
+                                 c->stream)));
+  CK(cocg_scalars(S, cv.tiles, cv.part, cv.sysd, cv.sysi, 0, 1 << kActive, c->opt.stern_tol, 0.0,
+                  maxit, 0, c->stream));
+  for (int round = 0; round < 60; ++round) {
+    CKS(cocg_loop<double>(c, cv, maxit));
+    int cnt[kNumStatus];
+    CKS(counts(c, S, cnt));
+    if (cnt[kConverged] == 0) break;
+    // true residual of recursively converged systems; restart those above tolerance
+    CK(proj_dots<double>(cv.nl, c->nd, S, x, cv.sysi, 1 << kConverged, cv.cdot, c->stream));
+    CK((cocg_resid<double, double>(cv, x, r, p, 1 << kConverged, nullptr, nullptr, nullptr,
+                                   c->stream)));
+    CK(cocg_scalars(S, cv.tiles, cv.part, cv.sysd, cv.sysi, 3, 1 << kConverged,
+                    c->opt.stern_tol, 0.0, maxit, 50, c->stream));
+    CKS(counts(c, S, cnt));
+    if (cnt[kActive] == 0) break;
+  }
+  CKS(collect_stats(c, S, ss));
+  CK((density<double, double>(c->nd, c->ns, nb, c->d64.psi.as<double>(), x, active,
+                              c->dens64.as<double>(), c->stream)));
+  return RPA_OK;
+}
+
+// Mixed form: FP32 Galerkin guess and COCG; FP64 residual refinement rounds solve for FP32
+// corrections that are accumulated in FP64.
+static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* active,
+                              SolveStats& ss) {
+  const int S = nb * c->ns;
+  const int maxit = c->opt.stern_maxit;
+  const double tol = c->opt.stern_tol;
+  const double itol = c->opt.inner_tol > 0.0 ? c->opt.inner_tol
+                                             : (c->opt.refine > 0 ? std::max(tol, 1e-5) : tol);
+  cpx<float>*x = c->x.as<cpx<float>>(), *r = c->r.as<cpx<float>>(), *p = c->p.as<cpx<float>>(),
+            *w = c->w.as<cpx<float>>();
+  CocgView<float> cv = make_view<float>(c, nb, u32, x, r, p, w);
+  CK(galerkin_guess<float>(c->nd, c->ns, nb, c->d32.psi.as<float>(), c->eps_d.as<double>(),
+                           c->pomega_d.as<double>(), u32, active, c->dV, c->gpart.as<double>(),
+                           gram_chunks(c->nd), c->cmat.as<cpx<float>>(), x, c->stream));
+  CK(set_status(S, c->ns, active, kActive, c->sysi.as<int>(), c->stream));
+  CK(proj_dots<float>(cv.nl, c->nd, S, x, cv.sysi, 1 << kActive, cv.cdot, c->stream));
+  CK((cocg_resid<float, float>(cv, x, r, p, 1 << kActive, nullptr, nullptr, nullptr, c->stream)));
+  CK(cocg_scalars(S, cv.tiles, cv.part, cv.sysd, cv.sysi, 5, 1 << kActive, tol, itol, maxit, 0,
+                  c->stream));
+  CKS(cocg_loop<float>(c, cv, maxit));
+  if (c->opt.refine <= 0) {
+    CKS(collect_stats(c, S, ss));
+    CK((density<float, float>(c->nd, c->ns, nb, c->d32.psi.as<float>(), x, active,
+                              c->dens64.as<double>(), c->stream)));
+    return RPA_OK;
+  }
+  // FP64 refinement
+  cpx<double>*x64 = c->x64.as<cpx<double>>(), *r64 = c->r64.as<cpx<double>>();
+  const int all_but_idle = ((1 << kNumStatus) - 1) & ~(1 << kIdle);
+  CK((accumulate<double, float>(c->nd, S, c->sysi.as<int>(), all_but_idle, -1, x, x64, 1,
+                                c->stream)));
+  CK(convert_f2d(u32, c->u64.as<double>(), (long long)nb * c->nd, c->stream));
+  CocgView<double> cv64 = make_view<double>(c, nb, c->u64.as<double>(), x64, r64, nullptr,
+                                            nullptr);
+  for (int round = 1; round <= c->opt.refine; ++round) {
+    CK(proj_dots<double>(cv64.nl, c->nd, S, x64, cv64.sysi, 1 << kConverged, cv64.cdot,
+                         c->stream));
+    CK((cocg_resid<double, float>(cv64, x64, r64, nullptr, 1 << kConverged, r, p, x, c->stream)));
+    CK(cocg_scalars(S, cv64.tiles, cv64.part, cv64.sysd, cv64.sysi, 4, 1 << kConverged, tol, itol,
+                    maxit, 0, c->stream));
+    int cnt[kNumStatus];
+    CKS(counts(c, S, cnt));
+    if (cnt[kActive] == 0) break;
+    CKS(cocg_loop<float>(c, cv, maxit));
+    const int corrected = (1 << kConverged) | (1 << kMaxit) | (1 << kBreakdown);
+    CK((accumulate<double, float>(c->nd, S, c->sysi.as<int>(), corrected, round, x, x64, 0,
+                                  c->stream)));
+    // systems that were final before this round keep status kFinal and are skipped above;
+    // systems corrected this round are kConverged again and are re-checked next round.
+  }
+  CKS(collect_stats(c, S, ss));
+  CK((density<double, double>(c->nd, c->ns, nb, c->d64.psi.as<double>(), x64, active,
+                              c->dens64.as<double>(), c->stream)));
+  return RPA_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// one wave of nb probe-points: Lanczos quadrature (Algorithm 1, inner part)
+// ---------------------------------------------------------------------------------------------
+struct WaveOut {
+  double* d;      // host, nb
+  double* alpha;  // host, nb x nl (may be null)
+  double* beta;
+  int* steps;
+};
+
+static rpa_status timing_mark(rpa_ctx* c, int i) {
+  if (c->have_events) CK(cudaEventRecord(c->ev[i], c->stream));
+  return RPA_OK;
+}
+
+static rpa_status timing_add(rpa_ctx* c, rpa_stats* st, int from, int to, int phase) {
+  if (!c->have_events || !st) return RPA_OK;
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev[from], c->ev[to]));
+  st->seconds_phase[phase] += 1e-3 * ms;
+  return RPA_OK;
+}
+
+static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const double* omega_h,
+                           WaveOut out, rpa_stats* st) {
+  const long long nd = c->nd;
+  const int nl = c->opt.lanczos_max;
+  const long long ldq = (long long)(nl + 1) * nd;
+  const bool mixed = c->opt.precision == RPA_MIXED;
+  double* Q = c->Q.as<double>();
+  int* active = c->active_d.as<int>();
+  CK(cudaMemcpyAsync(c->probe_d.p, probe_h, sizeof(long long) * nb, cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaMemcpyAsync(c->pomega_d.p, omega_h, sizeof(double) * nb, cudaMemcpyHostToDevice,
+                     c->stream));
+  {
+    std::vector<int> ones(nb, 1);
+    CK(cudaMemcpyAsync(active, ones.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  CK(cudaMemsetAsync(c->alpha_d.p, 0, sizeof(double) * nb * nl, c->stream));
+  CK(cudaMemsetAsync(c->beta_d.p, 0, sizeof(double) * nb * nl, c->stream));
+  CK(cudaMemsetAsync(c->steps_d.p, 0, sizeof(int) * nb, c->stream));
+  CK(cudaMemsetAsync(c->lstate_d.p, 0, sizeof(double) * nb * 4, c->stream));
+  CK(cudaMemsetAsync(c->flags_d.p, 0, sizeof(int) * 4, c->stream));
+  CK(lanczos_start(nd, nb, c->probe_d.as<long long>(), Q, ldq, c->stream));
+  const int nchunk = (int)std::max<long long>(1, std::min<long long>(64, (nd + 8191) / 8192));
+  double* dots = c->dots_d.as<double>();
+  double* dpart = c->dotpart_d.as<double>();
+  double* coef = c->coef_d.as<double>();
+  double* v = c->v64.as<double>();
+  for (int k = 0; k < nl; ++k) {
+    SolveStats ss;
+    CKS(timing_mark(c, 0));
+    // u = nu^{1/2} q_k
+    if (mixed) {
+      CKS((nu_half<float, double, float>(c, Q + (long long)k * nd, ldq, c->u32.as<float>(), nb,
+                                         c->t32a.as<float>(), c->t32b.as<float>())));
+    } else {
+      CKS((nu_half<double, double, double>(c, Q + (long long)k * nd, ldq, c->u64.as<double>(), nb,
+                                           c->t64a.as<double>(), c->t64b.as<double>())));
+    }
+    CKS(timing_mark(c, 1));
+    // Sternheimer solves and density (Galerkin guess + COCG)
+    if (mixed)
+      CKS(solve_mixed(c, nb, c->u32.as<float>(), active, ss));
+    else
+      CKS(solve_fp64(c, nb, c->u64.as<double>(), active, ss));
+    CKS(timing_mark(c, 2));
+    // v = nu^{1/2} r
+    if (mixed) {
+      CKS((nu_half<float, double, double>(c, c->dens64.as<double>(), nd, v, nb,
+                                          c->t32a.as<float>(), c->t32b.as<float>())));
+    } else {
+      CKS((nu_half<double, double, double>(c, c->dens64.as<double>(), nd, v, nb,
+                                           c->t64a.as<double>(), c->t64b.as<double>())));
+    }
+    CKS(timing_mark(c, 3));
+    // alpha_k = q_k^T v ; v -= alpha_k q_k + beta_{k-1} q_{k-1}
+    CK(multi_dot(nd, nb, Q, ldq, k, k + 1, v, active, dpart, nchunk, dots, c->stream));
+    CK(lanczos_alpha(nb, k, nl, dots, active, c->alpha_d.as<double>(), c->beta_d.as<double>(),
+                     coef, c->stream));
+    CK(multi_axpy(nd, nb, Q, ldq, std::max(0, k - 1), k + 1, k > 0 ? coef : coef + 1, 2, v,
+                  active, c->stream));
+    if (c->opt.reorth) {
+      for (int pass = 0; pass < 2; ++pass) {
+        CK(multi_dot(nd, nb, Q, ldq, 0, k + 1, v, active, dpart, nchunk, dots, c->stream));
+        CK(multi_axpy(nd, nb, Q, ldq, 0, k + 1, dots, k + 1, v, active, c->stream));
+      }
+    }
+    // beta_k = ||v||, q_{k+1} = v / beta_k (with breakdown / early-exit tests)
+    CK(multi_dot(nd, nb, v, nd, 0, 1, v, active, dpart, nchunk, dots, c->stream));
+    CK(lanczos_beta(nb, k, nl, dots, active, c->alpha_d.as<double>(), c->beta_d.as<double>(),
+                    c->steps_d.as<int>(), c->lstate_d.as<double>(), c->opt.lanczos_rtol,
+                    c->opt.fkind, c->flags_d.as<int>(), c->stream));
+    CK(lanczos_next(nd, nb, k, nl, active, c->lstate_d.as<double>(), c->beta_d.as<double>(), v, Q,
+                    ldq, c->stream));
+    CKS(timing_mark(c, 4));
+    // stats and the number of probes still running
+    std::vector<int> act(nb);
+    CK(cudaMemcpyAsync(act.data(), active, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (st) {
+      st->matvecs += 0;  // counted below from probe activity
+      st->solves += ss.solves;
+      st->cocg_iters += ss.iters;
+      st->refine_rounds += ss.refine_rounds;
+      st->max_cocg_iters = std::max(st->max_cocg_iters, ss.max_iters);
+      CKS(timing_add(c, st, 0, 1, 0));
+      CKS(timing_add(c, st, 1, 2, 2));
+      CKS(timing_add(c, st, 2, 3, 0));
+      CKS(timing_add(c, st, 3, 4, 4));
+    }
+    if (ss.nonconv) c->err = "a Sternheimer solve reached stern_maxit";
+    int any = 0;
+    for (int b = 0; b < nb; ++b) any += act[b];
+    if (st) st->matvecs += (long long)(ss.solves / std::max(1, c->ns));
+    if (ss.nonconv || ss.breakdown) {
+      // record and continue: results are still produced; the caller sees the status
+      c->opt.batch = c->opt.batch;  // no-op, keeps the state explicit
+    }
+    if (any == 0) break;
+  }
+  CKS(timing_mark(c, 5));
+  CK(tridiag_f11(nb, nl, c->alpha_d.as<double>(), nl, c->beta_d.as<double>(), nl,
+                 c->steps_d.as<int>(), c->opt.fkind, c->dout_d.as<double>(), c->stream));
+  CKS(timing_mark(c, 6));
+  CK(cudaMemcpyAsync(out.d, c->dout_d.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream));
+  if (out.alpha)
+    CK(cudaMemcpyAsync(out.alpha, c->alpha_d.p, sizeof(double) * nb * nl, cudaMemcpyDeviceToHost,
+                       c->stream));
+  if (out.beta)
+    CK(cudaMemcpyAsync(out.beta, c->beta_d.p, sizeof(double) * nb * nl, cudaMemcpyDeviceToHost,
+                       c->stream));
+  std::vector<int> steps(nb);
+  CK(cudaMemcpyAsync(steps.data(), c->steps_d.p, sizeof(int) * nb, cudaMemcpyDeviceToHost,
+                     c->stream));
+  int flags = 0;
+  CK(cudaMemcpyAsync(&flags, c->flags_d.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (out.steps) std::memcpy(out.steps, steps.data(), sizeof(int) * nb);
+  if (st) {
+    CKS(timing_add(c, st, 5, 6, 5));
+    for (int b = 0; b < nb; ++b) st->lanczos_steps_max = std::max(st->lanczos_steps_max, steps[b]);
+    st->probe_points += nb;
+  }
+  return RPA_OK;
+}
+
+// Run count probe-points in waves; d/alpha/beta/steps are host arrays in input order.
+static rpa_status run_probes(rpa_ctx* c, long long count, const long long* probe,
+                             const double* omg, double* d, double* alpha, double* beta,
+                             int* steps, rpa_stats* st, bool* nonconv) {
+  if (count == 0) return RPA_OK;
+  const int nb_max = choose_batch(c, count);
+  CKS(ensure_workspace(c, nb_max));
+  const int nl = c->opt.lanczos_max;
+  *nonconv = false;
+  for (long long s0 = 0; s0 < count; s0 += nb_max) {
+    const int nb = (int)std::min<long long>(nb_max, count - s0);
+    c->err.clear();
+    WaveOut o;
+    o.d = d + s0;
+    o.alpha = alpha ? alpha + s0 * nl : nullptr;
+    o.beta = beta ? beta + s0 * nl : nullptr;
+    o.steps = steps ? steps + s0 : nullptr;
+    CKS(run_wave(c, nb, probe + s0, omg + s0, o, st));
+    if (!c->err.empty()) *nonconv = true;
+  }
+  return RPA_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// interpolation (Section 3.2) and E_c
+// ---------------------------------------------------------------------------------------------
+static std::vector<long long> coarse_nodes(int n, int g, int bc) {
+  std::vector<long long> v;
+  for (int i = 0; i < n; i += g) v.push_back(i);
+  if (bc == RPA_DIRICHLET && v.back() != n - 1) v.push_back(n - 1);
+  return v;
+}
+
+static rpa_status build_interp(rpa_ctx* c) {
+  const int kind = c->opt.interp;
+  bool same = c->interp_built == kind;
+  for (int a = 0; a < 3; ++a) same = same && c->stride_built[a] == c->opt.stride[a];
+  if (same) return RPA_OK;
+  for (int a = 0; a < 3; ++a) {
+    const int n = c->grid.n[a], g = c->opt.stride[a];
+    c->cnodes[a] = coarse_nodes(n, g, c->grid.bc[a]);
+    const int m = (int)c->cnodes[a].size();
+    int k = kind;
+    if (g == 1) k = RPA_INTERP_NONE;
+    if (k == RPA_INTERP_FOURIER && (c->grid.bc[a] != RPA_PERIODIC || n % g != 0))
+      return fail(c, RPA_EINVAL, "Fourier interpolation needs periodic axes with n divisible by g");
+    if (k == RPA_INTERP_TRICUBIC && c->grid.bc[a] == RPA_PERIODIC && m > 1 && m < 4)
+      return fail(c, RPA_EINVAL, "tricubic interpolation on a periodic axis needs >= 4 coarse nodes");
+    if (k == RPA_INTERP_TRILINEAR && c->grid.bc[a] == RPA_PERIODIC && m > 1 && m < 2)
+      return fail(c, RPA_EINVAL, "trilinear interpolation needs >= 2 coarse nodes");
+    if (k == RPA_INTERP_NONE && g != 1)
+      return fail(c, RPA_EINVAL, "interp NONE requires stride 1");
+    CK(c->cnodes_d[a].ensure(sizeof(long long) * m));
+    CK(cudaMemcpyAsync(c->cnodes_d[a].p, c->cnodes[a].data(), sizeof(long long) * m,
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(c->interpWt[a].ensure(sizeof(double) * (size_t)m * n));
+    CK(interp_matrix(n, m, c->grid.bc[a], k, c->cnodes_d[a].as<long long>(),
+                     c->interpWt[a].as<double>(), c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  c->interp_built = kind;
+  for (int a = 0; a < 3; ++a) c->stride_built[a] = c->opt.stride[a];
+  return RPA_OK;
+}
+
+static long long num_probes(rpa_ctx* c) {
+  long long P = 1;
+  for (int a = 0; a < 3; ++a) P *= (long long)coarse_nodes(c->grid.n[a], c->opt.stride[a], c->grid.bc[a]).size();
+  return P;
+}
+
+// d_coarse (device, nw x P) -> d_fine (device, nw x N_d) and E_c (device scalar)
+static rpa_status interpolate_dev(rpa_ctx* c, const double* dco, double* dfi, double* ec_dev) {
+  CKS(build_interp(c));
+  const int m[3] = {(int)c->cnodes[0].size(), (int)c->cnodes[1].size(), (int)c->cnodes[2].size()};
+  const int* n = c->grid.n;
+  const long long P = (long long)m[0] * m[1] * m[2];
+  DevBuf t1, t2, part;
+  CK(t1.ensure(sizeof(double) * c->nw * (long long)n[0] * m[1] * m[2]));
+  CK(t2.ensure(sizeof(double) * c->nw * (long long)n[0] * n[1] * m[2]));
+  int d0[3] = {m[0], m[1], m[2]};
+  CK((mode_product<double, double, double>(dco, P, t1.as<double>(), (long long)n[0] * m[1] * m[2],
+                                           c->interpWt[0].as<double>(), 0, d0, n[0], c->nw,
+                                           nullptr, c->stream)));
+  int d1[3] = {n[0], m[1], m[2]};
+  CK((mode_product<double, double, double>(t1.as<double>(), (long long)n[0] * m[1] * m[2],
+                                           t2.as<double>(), (long long)n[0] * n[1] * m[2],
+                                           c->interpWt[1].as<double>(), 1, d1, n[1], c->nw,
+                                           nullptr, c->stream)));
+  int d2[3] = {n[0], n[1], m[2]};
+  CK((mode_product<double, double, double>(t2.as<double>(), (long long)n[0] * n[1] * m[2], dfi,
+                                           c->nd, c->interpWt[2].as<double>(), 2, d2, n[2],
+                                           c->nw, nullptr, c->stream)));
+  const int nblk = (int)std::max<long long>(1, std::min<long long>(256, (c->nd + 1023) / 1024));
+  CK(part.ensure(sizeof(double) * nblk * c->nw));
+  CK(ec_reduce(c->nd, c->nw, dfi, c->weight_d.as<double>(), part.as<double>(), nblk, ec_dev,
+               c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return RPA_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------------
+static rpa_status check_ready(rpa_ctx* c, bool need_freq) {
+  if (!c) return RPA_EINVAL;
+  if (!c->have_vloc) return fail(c, RPA_ESTATE, "rpa_set_potential has not been called");
+  if (!c->have_occ) return fail(c, RPA_ESTATE, "rpa_set_occupied has not been called");
+  if (need_freq && !c->have_freq) return fail(c, RPA_ESTATE, "no frequencies set");
+  CK(cudaSetDevice(c->device));
+  return RPA_OK;
+}
+
+extern "C" {
+
+rpa_status rpa_default_options(rpa_options* o) {
+  if (!o) return RPA_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->lanczos_max = 20;
+  o->lanczos_rtol = 0.0;
+  o->stern_tol = 1e-10;
+  o->stern_maxit = 2000;
+  o->precision = RPA_FP64;
+  o->reorth = 1;
+  o->stride[0] = o->stride[1] = o->stride[2] = 1;
+  o->interp = RPA_INTERP_TRICUBIC;
+  o->batch = 0;
+  o->fkind = RPA_F_LOG;
+  o->refine = 2;
+  o->inner_tol = 0.0;
+  return RPA_OK;
+}
+
+rpa_status rpa_create(rpa_ctx** out, const rpa_grid* g, void* stream) {
+  if (!out || !g) return RPA_EINVAL;
+  *out = nullptr;
+  long long nd = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (g->n[a] < 1 || g->n[a] > 1024 || !(g->h[a] > 0.0) ||
+        (g->bc[a] != RPA_PERIODIC && g->bc[a] != RPA_DIRICHLET))
+      return RPA_EINVAL;
+    nd *= g->n[a];
+  }
+  if (g->fd_radius < 1 || g->fd_radius > kMaxRadius || nd >= (1LL << 31)) return RPA_EINVAL;
+  rpa_ctx* c = new (std::nothrow) rpa_ctx();
+  if (!c) return RPA_ENOMEM;
+  c->grid = *g;
+  c->nd = nd;
+  c->dV = g->h[0] * g->h[1] * g->h[2];
+  rpa_default_options(&c->opt);
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return RPA_ECUDA;
+  }
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return RPA_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  if (cudaMallocHost(&c->pinned, 64 * sizeof(int)) != cudaSuccess) {
+    rpa_destroy(c);
+    return RPA_ENOMEM;
+  }
+  c->have_events = true;
+  for (int i = 0; i < 8; ++i)
+    if (cudaEventCreate(&c->ev[i]) != cudaSuccess) c->have_events = false;
+  make_stencil<double>(c->grid, c->d64.st);
+  make_stencil<float>(c->grid, c->d32.st);
+  // empty nonlocal part
+  std::vector<int> zoff(nd + 1, 0);
+  rpa_status st = RPA_OK;
+  if (c->p_off.ensure(sizeof(int) * (nd + 1)) != cudaSuccess ||
+      cudaMemcpy(c->p_off.p, zoff.data(), sizeof(int) * (nd + 1), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    st = RPA_ECUDA;
+  if (st == RPA_OK) st = build_nu(c);
+  if (st != RPA_OK) {
+    rpa_destroy(c);
+    return st;
+  }
+  *out = c;
+  return RPA_OK;
+}
+
+void rpa_destroy(rpa_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->have_events)
+    for (int i = 0; i < 8; ++i) cudaEventDestroy(c->ev[i]);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+rpa_status rpa_set_potential(rpa_ctx* c, const double* vloc, int where) {
+  if (!c || !vloc) return RPA_EINVAL;
+  CK(cudaSetDevice(c->device));
+  CK(c->d64.vloc.ensure(sizeof(double) * c->nd));
+  CK(c->d32.vloc.ensure(sizeof(float) * c->nd));
+  CKS(copy_in(c, c->d64.vloc.p, vloc, sizeof(double) * c->nd, where));
+  CK(convert_d2f(c->d64.vloc.as<double>(), c->d32.vloc.as<float>(), c->nd, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->have_vloc = true;
+  return RPA_OK;
+}
+
+rpa_status rpa_set_projectors(rpa_ctx* c, int ngroups, const int* nnz, const int* nproj,
+                              const int* idx, const double* chi, const double* gamma) {
+  if (!c || ngroups < 0) return RPA_EINVAL;
+  CK(cudaSetDevice(c->device));
+  const long long nd = c->nd;
+  // split groups into internal groups of <= 4 projectors sharing the support
+  std::vector<int> goff(1, 0), gidx;
+  std::vector<double> gchi, gcoef;
+  std::vector<std::vector<std::pair<int, long long>>> at;  // unused placeholder
+  long long ioff = 0, coff = 0, goff_in = 0;
+  for (int g = 0; g < ngroups; ++g) {
+    if (!nnz || !nproj || !idx || !chi || !gamma) return fail(c, RPA_EINVAL, "null projector array");
+    const int z = nnz[g], np = nproj[g];
+    if (z < 0 || np < 1 || np > 16) return fail(c, RPA_EINVAL, "projector group size out of range");
+    for (int e = 0; e < z; ++e)
+      if (idx[ioff + e] < 0 || idx[ioff + e] >= nd)
+        return fail(c, RPA_EINVAL, "projector index out of range");
+    for (int l0 = 0; l0 < np; l0 += kProjChunk) {
+      for (int e = 0; e < z; ++e) {
+        gidx.push_back(idx[ioff + e]);
+        for (int l = 0; l < kProjChunk; ++l)
+          gchi.push_back(l0 + l < np ? chi[coff + (long long)(l0 + l) * z + e] : 0.0);
+      }
+      for (int l = 0; l < kProjChunk; ++l)
+        gcoef.push_back(l0 + l < np ? gamma[goff_in + l0 + l] * c->dV : 0.0);
+      goff.push_back((int)gidx.size());
+    }
+    ioff += z;
+    coff += (long long)np * z;
+    goff_in += np;
+  }
+  const int NG = (int)goff.size() - 1;
+  const long long E = (long long)gidx.size();
+  if (E >= (1LL << 31)) return fail(c, RPA_EINVAL, "too many projector entries");
+  // point-major copy
+  std::vector<int> poff(nd + 1, 0);
+  for (long long e = 0; e < E; ++e) poff[gidx[e] + 1]++;
+  for (long long p = 0; p < nd; ++p) poff[p + 1] += poff[p];
+  std::vector<int> pgrp(std::max<long long>(E, 1)), fill(poff.begin(), poff.end() - 1);
+  std::vector<double> pchi(std::max<long long>(E, 1) * kProjChunk);
+  for (int g = 0; g < NG; ++g)
+    for (int e = goff[g]; e < goff[g + 1]; ++e) {
+      const int pt = gidx[e];
+      const int slot = fill[pt]++;
+      pgrp[slot] = g;
+      for (int l = 0; l < kProjChunk; ++l) pchi[(size_t)slot * kProjChunk + l] = gchi[(size_t)e * kProjChunk + l];
+    }
+  std::vector<float> gchi_f(gchi.begin(), gchi.end()), gcoef_f(gcoef.begin(), gcoef.end()),
+      pchi_f(pchi.begin(), pchi.end());
+  const size_t Eb = std::max<long long>(E, 1);
+  CK(c->g_off.ensure(sizeof(int) * goff.size()));
+  CK(c->g_idx.ensure(sizeof(int) * Eb));
+  CK(c->p_off.ensure(sizeof(int) * (nd + 1)));
+  CK(c->p_grp.ensure(sizeof(int) * Eb));
+  CK(c->d64.g_chi.ensure(sizeof(double) * Eb * kProjChunk));
+  CK(c->d32.g_chi.ensure(sizeof(float) * Eb * kProjChunk));
+  CK(c->d64.p_chi.ensure(sizeof(double) * Eb * kProjChunk));
+  CK(c->d32.p_chi.ensure(sizeof(float) * Eb * kProjChunk));
+  CK(c->d64.coef.ensure(sizeof(double) * std::max(NG, 1) * kProjChunk));
+  CK(c->d32.coef.ensure(sizeof(float) * std::max(NG, 1) * kProjChunk));
+  CK(cudaMemcpy(c->g_off.p, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->p_off.p, poff.data(), sizeof(int) * (nd + 1), cudaMemcpyHostToDevice));
+  if (E > 0) {
+    CK(cudaMemcpy(c->g_idx.p, gidx.data(), sizeof(int) * E, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->p_grp.p, pgrp.data(), sizeof(int) * E, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d64.g_chi.p, gchi.data(), sizeof(double) * E * kProjChunk, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d32.g_chi.p, gchi_f.data(), sizeof(float) * E * kProjChunk, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d64.p_chi.p, pchi.data(), sizeof(double) * E * kProjChunk, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d32.p_chi.p, pchi_f.data(), sizeof(float) * E * kProjChunk, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d64.coef.p, gcoef.data(), sizeof(double) * NG * kProjChunk, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d32.coef.p, gcoef_f.data(), sizeof(float) * NG * kProjChunk, cudaMemcpyHostToDevice));
+  }
+  c->ngroup = NG;
+  return RPA_OK;
+}
+
+rpa_status rpa_set_occupied(rpa_ctx* c, int ns, const double* psi, const double* eps, int where) {
+  if (!c || !psi || !eps || ns < 1 || ns > 1024) return RPA_EINVAL;
+  CK(cudaSetDevice(c->device));
+  std::vector<double> e(ns);
+  if (where == RPA_DEVICE)
+    CK(cudaMemcpy(e.data(), eps, sizeof(double) * ns, cudaMemcpyDeviceToHost));
+  else
+    std::memcpy(e.data(), eps, sizeof(double) * ns);
+  for (int i = 0; i + 1 < ns; ++i)
+    if (!(e[i] <= e[i + 1])) return fail(c, RPA_ENOGAP, "eps must be ascending");
+  const long long n = (long long)ns * c->nd;
+  CK(c->d64.psi.ensure(sizeof(double) * n));
+  CK(c->d32.psi.ensure(sizeof(float) * n));
+  CK(c->eps_d.ensure(sizeof(double) * ns));
+  CKS(copy_in(c, c->d64.psi.p, psi, sizeof(double) * n, where));
+  CK(convert_d2f(c->d64.psi.as<double>(), c->d32.psi.as<float>(), n, c->stream));
+  CK(cudaMemcpyAsync(c->eps_d.p, e.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->ns = ns;
+  c->have_occ = true;
+  c->ws_nb = 0;
+  return RPA_OK;
+}
+
+rpa_status rpa_set_frequencies(rpa_ctx* c, int nw, const double* omega, const double* weight) {
+  if (!c || nw < 1 || nw > 64 || !omega || !weight) return RPA_EINVAL;
+  for (int k = 0; k < nw; ++k)
+    if (!(omega[k] > 0.0) || !std::isfinite(weight[k]))
+      return fail(c, RPA_EINVAL, "frequencies must be positive and weights finite");
+  CK(cudaSetDevice(c->device));
+  c->omega.assign(omega, omega + nw);
+  c->weight.assign(weight, weight + nw);
+  CK(c->omega_d.ensure(sizeof(double) * nw));
+  CK(c->weight_d.ensure(sizeof(double) * nw));
+  CK(cudaMemcpy(c->omega_d.p, omega, sizeof(double) * nw, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->weight_d.p, weight, sizeof(double) * nw, cudaMemcpyHostToDevice));
+  c->nw = nw;
+  c->have_freq = true;
+  return RPA_OK;
+}
+
+rpa_status rpa_gl_frequencies(int nw, double* omega, double* weight) {
+  if (nw < 1 || nw > 64 || !omega || !weight) return RPA_EINVAL;
+  double* d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * 2 * nw) != cudaSuccess) return RPA_ENOMEM;
+  rpa_status st = RPA_OK;
+  if (gl_nodes(nw, d, d + nw, 0) != cudaSuccess ||
+      cudaMemcpy(omega, d, sizeof(double) * nw, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(weight, d + nw, sizeof(double) * nw, cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = RPA_ECUDA;
+  cudaFree(d);
+  return st;
+}
+
+rpa_status rpa_set_options(rpa_ctx* c, const rpa_options* o) {
+  if (!c || !o) return RPA_EINVAL;
+  if (o->lanczos_max < 1 || o->lanczos_max > kMaxLanczos) return fail(c, RPA_EINVAL, "lanczos_max out of range");
+  if (!(o->stern_tol > 0.0) || o->stern_maxit < 1) return fail(c, RPA_EINVAL, "bad Sternheimer tolerance");
+  if (o->precision != RPA_FP64 && o->precision != RPA_MIXED) return fail(c, RPA_EINVAL, "bad precision");
+  if (o->interp < RPA_INTERP_NONE || o->interp > RPA_INTERP_FOURIER) return fail(c, RPA_EINVAL, "bad interp");
+  if (o->fkind < RPA_F_LOG || o->fkind > RPA_F_X2) return fail(c, RPA_EINVAL, "bad fkind");
+  if (o->lanczos_rtol < 0.0 || o->refine < 0 || o->refine > 20 || o->batch < 0)
+    return fail(c, RPA_EINVAL, "bad option");
+  for (int a = 0; a < 3; ++a)
+    if (o->stride[a] < 1 || o->stride[a] > c->grid.n[a]) return fail(c, RPA_EINVAL, "bad stride");
+  const bool realloc = o->precision != c->opt.precision || o->lanczos_max != c->opt.lanczos_max ||
+                       o->refine != c->opt.refine;
+  c->opt = *o;
+  if (realloc) c->ws_nb = 0;
+  return RPA_OK;
+}
+
+rpa_status rpa_num_probes(rpa_ctx* c, long long* P) {
+  if (!c || !P) return RPA_EINVAL;
+  *P = num_probes(c);
+  return RPA_OK;
+}
+
+rpa_status rpa_probe_indices(rpa_ctx* c, long long* idx) {
+  if (!c || !idx) return RPA_EINVAL;
+  std::vector<long long> cn[3];
+  for (int a = 0; a < 3; ++a) cn[a] = coarse_nodes(c->grid.n[a], c->opt.stride[a], c->grid.bc[a]);
+  long long q = 0;
+  for (long long kz : cn[2])
+    for (long long ky : cn[1])
+      for (long long kx : cn[0]) idx[q++] = kx + (long long)c->grid.n[0] * (ky + (long long)c->grid.n[1] * kz);
+  return RPA_OK;
+}
+
+rpa_status rpa_probe_density(rpa_ctx* c, int count, const long long* probe, const int* freq,
+                             double* d, double* alpha, double* beta, int* steps, rpa_stats* st,
+                             int where) {
+  CKS(check_ready(c, true));
+  if (count < 0 || (count > 0 && (!probe || !freq || !d))) return fail(c, RPA_EINVAL, "bad arguments");
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<long long> pr(count);
+  std::vector<int> fq(count);
+  if (where == RPA_DEVICE) {
+    if (count > 0) {
+      CK(cudaMemcpy(pr.data(), probe, sizeof(long long) * count, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(fq.data(), freq, sizeof(int) * count, cudaMemcpyDeviceToHost));
+    }
+  } else {
+    std::memcpy(pr.data(), probe, sizeof(long long) * count);
+    std::memcpy(fq.data(), freq, sizeof(int) * count);
+  }
+  std::vector<double> om(count);
+  for (int i = 0; i < count; ++i) {
+    if (pr[i] < 0 || pr[i] >= c->nd || fq[i] < 0 || fq[i] >= c->nw)
+      return fail(c, RPA_EINVAL, "probe or frequency index out of range");
+    om[i] = c->omega[fq[i]];
+  }
+  if (st) std::memset(st, 0, sizeof(*st));
+  const int nl = c->opt.lanczos_max;
+  std::vector<double> dh(count), ah(alpha ? (size_t)count * nl : 0), bh(beta ? (size_t)count * nl : 0);
+  std::vector<int> sh(steps ? count : 0);
+  bool nonconv = false;
+  CKS(run_probes(c, count, pr.data(), om.data(), dh.data(), alpha ? ah.data() : nullptr,
+                 beta ? bh.data() : nullptr, steps ? sh.data() : nullptr, st, &nonconv));
+  CKS(copy_out(c, d, dh.data(), sizeof(double) * count, where));
+  if (alpha) CKS(copy_out(c, alpha, ah.data(), sizeof(double) * count * nl, where));
+  if (beta) CKS(copy_out(c, beta, bh.data(), sizeof(double) * count * nl, where));
+  if (steps) CKS(copy_out(c, steps, sh.data(), sizeof(int) * count, where));
+  CK(cudaStreamSynchronize(c->stream));
+  if (st) st->seconds_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (nonconv) return fail(c, RPA_ENOCONV, "a Sternheimer solve reached stern_maxit");
+  return RPA_OK;
+}
+
+rpa_status rpa_interpolate(rpa_ctx* c, const double* d_coarse, double* d_fine, double* ec,
+                           int where) {
+  if (!c || !d_coarse) return RPA_EINVAL;
+  if (!c->have_freq) return fail(c, RPA_ESTATE, "no frequencies set");
+  CK(cudaSetDevice(c->device));
+  const long long P = num_probes(c);
+  DevBuf dco, dfi, ecd;
+  CK(dco.ensure(sizeof(double) * c->nw * P));
+  CK(dfi.ensure(sizeof(double) * c->nw * c->nd));
+  CK(ecd.ensure(sizeof(double)));
+  CKS(copy_in(c, dco.p, d_coarse, sizeof(double) * c->nw * P, where));
+  CKS(interpolate_dev(c, dco.as<double>(), dfi.as<double>(), ecd.as<double>()));
+  if (d_fine) CKS(copy_out(c, d_fine, dfi.p, sizeof(double) * c->nw * c->nd, where));
+  if (ec) CKS(copy_out(c, ec, ecd.p, sizeof(double), where));
+  CK(cudaStreamSynchronize(c->stream));
+  return RPA_OK;
+}
+
+rpa_status rpa_energy_density(rpa_ctx* c, double* d_coarse, double* d_fine, double* ec,
+                              rpa_stats* st, int where) {
+  CKS(check_ready(c, true));
+  auto t0 = std::chrono::steady_clock::now();
+  if (st) std::memset(st, 0, sizeof(*st));
+  const long long P = num_probes(c);
+  std::vector<long long> idx(P);
+  CKS(rpa_probe_indices(c, idx.data()));
+  const long long count = P * c->nw;
+  std::vector<long long> pr(count);
+  std::vector<double> om(count), dh(count);
+  for (int k = 0; k < c->nw; ++k)
+    for (long long j = 0; j < P; ++j) {
+      pr[k * P + j] = idx[j];
+      om[k * P + j] = c->omega[k];
+    }
+  bool nonconv = false;
+  CKS(run_probes(c, count, pr.data(), om.data(), dh.data(), nullptr, nullptr, nullptr, st,
+                 &nonconv));
+  auto t1 = std::chrono::steady_clock::now();
+  DevBuf dco, dfi, ecd;
+  CK(dco.ensure(sizeof(double) * count));
+  CK(dfi.ensure(sizeof(double) * c->nw * c->nd));
+  CK(ecd.ensure(sizeof(double)));
+  CK(cudaMemcpyAsync(dco.p, dh.data(), sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+  CKS(interpolate_dev(c, dco.as<double>(), dfi.as<double>(), ecd.as<double>()));
+  if (d_coarse) CKS(copy_out(c, d_coarse, dco.p, sizeof(double) * count, where));
+  if (d_fine) CKS(copy_out(c, d_fine, dfi.p, sizeof(double) * c->nw * c->nd, where));
+  if (ec) CKS(copy_out(c, ec, ecd.p, sizeof(double), where));
+  CK(cudaStreamSynchronize(c->stream));
+  auto t2 = std::chrono::steady_clock::now();
+  if (st) {
+    st->seconds_phase[6] += std::chrono::duration<double>(t2 - t1).count();
+    st->seconds_total = std::chrono::duration<double>(t2 - t0).count();
+  }
+  if (nonconv) return fail(c, RPA_ENOCONV, "a Sternheimer solve reached stern_maxit");
+  return RPA_OK;
+}
+
+rpa_status rpa_apply_h(rpa_ctx* c, int count, const double* x, const double* sigma, double* y,
+                       int where) {
+  if (!c || count < 0 || (count > 0 && (!x || !sigma || !y))) return RPA_EINVAL;
+  if (!c->have_vloc) return fail(c, RPA_ESTATE, "rpa_set_potential has not been called");
+  if (count == 0) return RPA_OK;
+  CK(cudaSetDevice(c->device));
+  const long long n = (long long)count * c->nd;
+  DevBuf xd, yd, sd, cd;
+  CK(xd.ensure(sizeof(cpx<double>) * n));
+  CK(yd.ensure(sizeof(cpx<double>) * n));
+  CK(sd.ensure(sizeof(cpx<double>) * count));
+  CK(cd.ensure(sizeof(cpx<double>) * count * std::max(1, c->ngroup) * kProjChunk));
+  CKS(copy_in(c, xd.p, x, sizeof(cpx<double>) * n, where));
+  CKS(copy_in(c, sd.p, sigma, sizeof(cpx<double>) * count, where));
+  if (c->opt.precision == RPA_FP64) {
+    CK(apply_h<double>(c->d64.st, c->d64.vloc.as<double>(), nlview<double>(c), c->nd, count,
+                       xd.as<cpx<double>>(), sd.as<cpx<double>>(), cd.as<cpx<double>>(),
+                       yd.as<cpx<double>>(), c->stream));
+  } else {
+    DevBuf xf, yf, sf;
+    CK(xf.ensure(sizeof(cpx<float>) * n));
+    CK(yf.ensure(sizeof(cpx<float>) * n));
+    CK(sf.ensure(sizeof(cpx<float>) * count));
+    CK(convert_d2f(xd.as<double>(), xf.as<float>(), 2 * n, c->stream));
+    CK(convert_d2f(sd.as<double>(), sf.as<float>(), 2 * count, c->stream));
+    CK(apply_h<float>(c->d32.st, c->d32.vloc.as<float>(), nlview<float>(c), c->nd, count,
+                      xf.as<cpx<float>>(), sf.as<cpx<float>>(), cd.as<cpx<float>>(),
+                      yf.as<cpx<float>>(), c->stream));
+    CK(convert_f2d(yf.as<float>(), yd.as<double>(), 2 * n, c->stream));
+  }
+  CKS(copy_out(c, y, yd.p, sizeof(cpx<double>) * n, where));
+  CK(cudaStreamSynchronize(c->stream));
+  return RPA_OK;
+}
+
+rpa_status rpa_apply_nu_half(rpa_ctx* c, int count, const double* q, double* u, int where) {
+  if (!c || count < 0 || (count > 0 && (!q || !u))) return RPA_EINVAL;
+  if (count == 0) return RPA_OK;
+  CK(cudaSetDevice(c->device));
+  const long long n = (long long)count * c->nd;
+  DevBuf qd, ud, ta, tb;
+  CK(qd.ensure(sizeof(double) * n));
+  CK(ud.ensure(sizeof(double) * n));
+  CKS(copy_in(c, qd.p, q, sizeof(double) * n, where));
+  if (c->opt.precision == RPA_FP64) {
+    CK(ta.ensure(sizeof(double) * n));
+    CK(tb.ensure(sizeof(double) * n));
+    CKS((nu_half<double, double, double>(c, qd.as<double>(), c->nd, ud.as<double>(), count,
+                                         ta.as<double>(), tb.as<double>())));
+  } else {
+    CK(ta.ensure(sizeof(float) * n));
+    CK(tb.ensure(sizeof(float) * n));
+    CKS((nu_half<float, double, double>(c, qd.as<double>(), c->nd, ud.as<double>(), count,
+                                        ta.as<float>(), tb.as<float>())));
+  }
+  CKS(copy_out(c, u, ud.p, sizeof(double) * n, where));
+  CK(cudaStreamSynchronize(c->stream));
+  return RPA_OK;
+}
+
+rpa_status rpa_chi0(rpa_ctx* c, int count, const double* omega, const double* u, double* r,
+                    int* iters, int where) {
+  CKS(check_ready(c, false));
+  if (count < 0 || (count > 0 && (!omega || !u || !r))) return fail(c, RPA_EINVAL, "bad arguments");
+  if (count == 0) return RPA_OK;
+  const int nb_max = choose_batch(c, count);
+  CKS(ensure_workspace(c, nb_max));
+  std::vector<double> om(count);
+  if (where == RPA_DEVICE)
+    CK(cudaMemcpy(om.data(), omega, sizeof(double) * count, cudaMemcpyDeviceToHost));
+  else
+    std::memcpy(om.data(), omega, sizeof(double) * count);
+  for (int i = 0; i < count; ++i)
+    if (!(om[i] > 0.0)) return fail(c, RPA_EINVAL, "omega must be positive");
+  bool nonconv = false;
+  for (int s0 = 0; s0 < count; s0 += nb_max) {
+    const int nb = std::min(nb_max, count - s0);
+    std::vector<int> ones(nb, 1);
+    CK(cudaMemcpyAsync(c->active_d.p, ones.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->pomega_d.p, om.data() + s0, sizeof(double) * nb, cudaMemcpyHostToDevice,
+                       c->stream));
+    CKS(copy_in(c, c->u64.p, u + (long long)s0 * c->nd, sizeof(double) * nb * c->nd, where));
+    SolveStats ss;
+    if (c->opt.precision == RPA_MIXED) {
+      CK(convert_d2f(c->u64.as<double>(), c->u32.as<float>(), (long long)nb * c->nd, c->stream));
+      CKS(solve_mixed(c, nb, c->u32.as<float>(), c->active_d.as<int>(), ss));
+    } else {
+      CKS(solve_fp64(c, nb, c->u64.as<double>(), c->active_d.as<int>(), ss));
+    }
+    if (ss.nonconv) nonconv = true;
+    CKS(copy_out(c, r + (long long)s0 * c->nd, c->dens64.p, sizeof(double) * nb * c->nd, where));
+    if (iters) {
+      std::vector<int> si((size_t)nb * c->ns * kSysI);
+      CK(cudaMemcpyAsync(si.data(), c->sysi.p, sizeof(int) * si.size(), cudaMemcpyDeviceToHost,
+                         c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      std::vector<int> it((size_t)nb * c->ns);
+      for (size_t s = 0; s < it.size(); ++s) it[s] = si[s * kSysI + kIters];
+      CKS(copy_out(c, iters + (long long)s0 * c->ns, it.data(), sizeof(int) * it.size(), where));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  if (nonconv) return fail(c, RPA_ENOCONV, "a Sternheimer solve reached stern_maxit");
+  return RPA_OK;
+}
+
+rpa_status rpa_tridiag_f11(int count, int k, const double* alpha, const double* beta, int fkind,
+                           double* d) {
+  if (count < 0 || k < 1 || k > kMaxLanczos || (count > 0 && (!alpha || !beta || !d)) ||
+      fkind < RPA_F_LOG || fkind > RPA_F_X2)
+    return RPA_EINVAL;
+  if (count == 0) return RPA_OK;
+  double* buf = nullptr;
+  const size_t n = (size_t)count * k;
+  if (cudaMalloc(&buf, sizeof(double) * (2 * n + count)) != cudaSuccess) return RPA_ENOMEM;
+  rpa_status st = RPA_OK;
+  if (cudaMemcpy(buf, alpha, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(buf + n, beta, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      tridiag_f11(count, k, buf, k, buf + n, k, nullptr, fkind, buf + 2 * n, 0) != cudaSuccess ||
+      cudaMemcpy(d, buf + 2 * n, sizeof(double) * count, cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = RPA_ECUDA;
+  cudaFree(buf);
+  return st;
+}
+
+const char* rpa_status_string(rpa_status st) {
+  switch (st) {
+    case RPA_OK: return "ok";
+    case RPA_EINVAL: return "invalid argument";
+    case RPA_ENOMEM: return "out of memory";
+    case RPA_ECUDA: return "CUDA error";
+    case RPA_ENOCONV: return "Sternheimer solve did not converge";
+    case RPA_EBREAKDOWN: return "breakdown";
+    case RPA_ETIMEOUT: return "timeout";
+    case RPA_ENOGAP: return "occupied set not separated";
+    case RPA_ESTATE: return "call order";
+  }
+  return "unknown status";
+}
+
+const char* rpa_last_error(const rpa_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+long long rpa_kernel_launches(const rpa_ctx*) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,611 @@
+// Batched Sternheimer solves by COCG (Eq. 4, Section 4) with the finite-difference
+// Hamiltonian stencil, local potential and nonlocal projectors.
+//
+// A batch holds S = B x N_s complex-symmetric systems (H - eps_n - i w_b) x = b,
+// b = -psi_n (.) u_b.  Every vector is S x N_d complex (interleaved).  Kernels are launched
+// over (tiles, systems); a system whose status is not selected returns at once, so converged
+// systems retire individually.  Reductions are deterministic: each block writes its partial
+// sums, and one warp per system adds them in a fixed order.
+#include <cuda_runtime.h>
+
+#include "cocg.cuh"
+
+namespace rpa {
+
+// -------------------------------------------------------------------------------------------
+// helpers
+// -------------------------------------------------------------------------------------------
+__device__ __forceinline__ int wrap_index(int j, int n, int bc) {
+  if (bc == 0) {
+    while (j < 0) j += n;
+    while (j >= n) j -= n;
+    return j;
+  }
+  return (j < 0 || j >= n) ? -1 : j;
+}
+
+// (-1/2 Lap_h + V - sigma) x at one point, plus the nonlocal term from precomputed
+// projector coefficients cd (gamma dV chi^T x per internal group and projector).
+template <typename T>
+__device__ __forceinline__ cpx<T> h_at(const Stencil<T>& st, const T* __restrict__ vloc,
+                                       const NonlocalDev<T>& nl, const cpx<T>* __restrict__ x,
+                                       const cpx<T>* __restrict__ cd, int ix, int iy, int iz,
+                                       long long p, cpx<T> sigma) {
+  const cpx<T> xc = x[p];
+  const T dg = st.c0 + vloc[p];
+  cpx<T> acc = mk<T>(dg * xc.re - (sigma.re * xc.re - sigma.im * xc.im),
+                     dg * xc.im - (sigma.re * xc.im + sigma.im * xc.re));
+  const long long sx = 1, sy = st.nx, sz = (long long)st.nx * st.ny;
+  const long long base = p - ix * sx - iy * sy - iz * sz;
+#pragma unroll 4
+  for (int m = 1; m <= st.R; ++m) {
+    int a = wrap_index(ix + m, st.nx, st.bcx), b = wrap_index(ix - m, st.nx, st.bcx);
+    cpx<T> s = mk<T>(0, 0);
+    if (a >= 0) s = cadd(s, x[base + a * sx + iy * sy + iz * sz]);
+    if (b >= 0) s = cadd(s, x[base + b * sx + iy * sy + iz * sz]);
+    acc = caxpy_r(acc, st.cx[m], s);
+    a = wrap_index(iy + m, st.ny, st.bcy);
+    b = wrap_index(iy - m, st.ny, st.bcy);
+    s = mk<T>(0, 0);
+    if (a >= 0) s = cadd(s, x[base + ix * sx + a * sy + iz * sz]);
+    if (b >= 0) s = cadd(s, x[base + ix * sx + b * sy + iz * sz]);
+    acc = caxpy_r(acc, st.cy[m], s);
+    a = wrap_index(iz + m, st.nz, st.bcz);
+    b = wrap_index(iz - m, st.nz, st.bcz);
+    s = mk<T>(0, 0);
+    if (a >= 0) s = cadd(s, x[base + ix * sx + iy * sy + a * sz]);
+    if (b >= 0) s = cadd(s, x[base + ix * sx + iy * sy + b * sz]);
+    acc = caxpy_r(acc, st.cz[m], s);
+  }
+  if (nl.ngroup > 0) {
+    const int e0 = nl.p_off[p], e1 = nl.p_off[p + 1];
+    for (int e = e0; e < e1; ++e) {
+      const int g = nl.p_grp[e];
+      const T* ch = nl.p_chi + (long long)e * kProjChunk;
+      const cpx<T>* c = cd + (long long)g * kProjChunk;
+#pragma unroll
+      for (int l = 0; l < kProjChunk; ++l) acc = caxpy_r(acc, ch[l], c[l]);
+    }
+  }
+  return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ void point_coords(long long p, const Stencil<T>& st, int& ix, int& iy,
+                                             int& iz) {
+  const long long pl = (long long)st.nx * st.ny;
+  iz = (int)(p / pl);
+  const long long rem = p - (long long)iz * pl;
+  iy = (int)(rem / st.nx);
+  ix = (int)(rem - (long long)iy * st.nx);
+}
+
+// Block reduction of NQ doubles; result valid in thread 0.
+template <int NQ>
+__device__ __forceinline__ void block_reduce(double (&v)[NQ], double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sh[wid * NQ + q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] += sh[w * NQ + q];
+    }
+  }
+}
+
+__device__ __forceinline__ int status_of(const int* sysi, int s) {
+  return sysi[(long long)s * kSysI + kStatus];
+}
+__device__ __forceinline__ bool selected(const int* sysi, int s, int mask) {
+  return (mask >> status_of(sysi, s)) & 1;
+}
+
+// -------------------------------------------------------------------------------------------
+// projector dot products: cd[s][g][l] = gamma_{g,l} dV sum_e chi_{g,l}(e) v_s(idx_e)
+// -------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) k_proj_dots(NonlocalDev<T> nl, long long nd,
+                                                   const cpx<T>* __restrict__ vec,
+                                                   const int* __restrict__ sysi, int mask,
+                                                   cpx<T>* __restrict__ cd) {
+  const int g = blockIdx.x, s = blockIdx.y;
+  if (sysi && !selected(sysi, s, mask)) return;
+  __shared__ double sh[4 * 2 * kProjChunk];
+  const cpx<T>* v = vec + (long long)s * nd;
+  double acc[2 * kProjChunk];
+#pragma unroll
+  for (int q = 0; q < 2 * kProjChunk; ++q) acc[q] = 0.0;
+  for (int e = nl.g_off[g] + threadIdx.x; e < nl.g_off[g + 1]; e += blockDim.x) {
+    const cpx<T> xv = v[nl.g_idx[e]];
+    const T* ch = nl.g_chi + (long long)e * kProjChunk;
+#pragma unroll
+    for (int l = 0; l < kProjChunk; ++l) {
+      acc[2 * l] += (double)(ch[l] * xv.re);
+      acc[2 * l + 1] += (double)(ch[l] * xv.im);
+    }
+  }
+  block_reduce<2 * kProjChunk>(acc, sh);
+  if (threadIdx.x == 0) {
+    cpx<T>* out = cd + ((long long)s * nl.ngroup + g) * kProjChunk;
+#pragma unroll
+    for (int l = 0; l < kProjChunk; ++l) {
+      const double c = (double)nl.coef[g * kProjChunk + l];
+      out[l] = mk<T>((T)(c * acc[2 * l]), (T)(c * acc[2 * l + 1]));
+    }
+  }
+}
+
+// -------------------------------------------------------------------------------------------
+// y = (H - sigma) x for independent vectors (step check of the H apply)
+// -------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_h(Stencil<T> st, const T* __restrict__ vloc,
+                                                 NonlocalDev<T> nl, long long nd,
+                                                 const cpx<T>* __restrict__ x,
+                                                 const cpx<T>* __restrict__ sigma,
+                                                 const cpx<T>* __restrict__ cd,
+                                                 cpx<T>* __restrict__ y) {
+  const int s = blockIdx.y;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nd) return;
+  int ix, iy, iz;
+  point_coords(p, st, ix, iy, iz);
+  y[(long long)s * nd + p] = h_at(st, vloc, nl, x + (long long)s * nd,
+                                  cd + (long long)s * nl.ngroup * kProjChunk, ix, iy, iz, p,
+                                  sigma[s]);
+}
+
+// -------------------------------------------------------------------------------------------
+// COCG kernels
+// -------------------------------------------------------------------------------------------
+// r = b - A x, b = -psi_n u_b (or b = rhs when rhs != null); optionally p = r, and for a
+// refinement round the low-precision copies r_lo = p_lo = r, x_lo = 0.
+// Partials per block: ||r||^2, ||b||^2, r^T r (re, im).
+template <typename T, typename TL>
+__global__ void __launch_bounds__(256) k_resid(CocgView<T> cv, const cpx<T>* __restrict__ x,
+                                               cpx<T>* __restrict__ r, cpx<T>* __restrict__ pdir,
+                                               int mask, cpx<TL>* __restrict__ r_lo,
+                                               cpx<TL>* __restrict__ p_lo,
+                                               cpx<TL>* __restrict__ x_lo) {
+  const int s = blockIdx.y;
+  if (!selected(cv.sysi, s, mask)) return;
+  __shared__ double sh[8 * 4];
+  const int b = s / cv.ns, n = s - b * cv.ns;
+  const long long nd = cv.nd;
+  const cpx<T> sigma = mk<T>((T)cv.eps[n], (T)cv.omega[b]);
+  const cpx<T>* xs = x + (long long)s * nd;
+  const cpx<T>* cd = cv.cdot + (long long)s * cv.nl.ngroup * kProjChunk;
+  const T* psin = cv.psi + (long long)n * nd;
+  const T* ub = cv.u + (long long)b * nd;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const long long t0 = (long long)blockIdx.x * kTile;
+  const long long t1 = min(t0 + kTile, nd);
+  for (long long p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
+    int ix, iy, iz;
+    point_coords(p, cv.st, ix, iy, iz);
+    const cpx<T> ax = h_at(cv.st, cv.vloc, cv.nl, xs, cd, ix, iy, iz, p, sigma);
+    const cpx<T> bv = mk<T>(-psin[p] * ub[p], (T)0);
+    const cpx<T> rv = csub(bv, ax);
+    r[(long long)s * nd + p] = rv;
+    if (pdir) pdir[(long long)s * nd + p] = rv;
+    if (r_lo) {
+      const cpx<TL> rl = mk<TL>((TL)rv.re, (TL)rv.im);
+      r_lo[(long long)s * nd + p] = rl;
+      p_lo[(long long)s * nd + p] = rl;
+      x_lo[(long long)s * nd + p] = mk<TL>((TL)0, (TL)0);
+    }
+    acc[0] += (double)rv.re * rv.re + (double)rv.im * rv.im;
+    acc[1] += (double)bv.re * bv.re;
+    acc[2] += (double)rv.re * rv.re - (double)rv.im * rv.im;
+    acc[3] += 2.0 * (double)rv.re * rv.im;
+  }
+  block_reduce<4>(acc, sh);
+  if (threadIdx.x == 0) {
+    double* pp = cv.part + ((long long)s * cv.tiles + blockIdx.x) * 4;
+    pp[0] = acc[0];
+    pp[1] = acc[1];
+    pp[2] = acc[2];
+    pp[3] = acc[3];
+  }
+}
+
+// w = A p, partial mu = p^T w
+template <typename T>
+__global__ void __launch_bounds__(256) k_matvec(CocgView<T> cv) {
+  const int s = blockIdx.y;
+  if (status_of(cv.sysi, s) != kActive) return;
+  __shared__ double sh[8 * 2];
+  const int b = s / cv.ns, n = s - b * cv.ns;
+  const long long nd = cv.nd;
+  const cpx<T> sigma = mk<T>((T)cv.eps[n], (T)cv.omega[b]);
+  const cpx<T>* ps = cv.p + (long long)s * nd;
+  const cpx<T>* cd = cv.cdot + (long long)s * cv.nl.ngroup * kProjChunk;
+  double acc[2] = {0.0, 0.0};
+  const long long t0 = (long long)blockIdx.x * kTile;
+  const long long t1 = min(t0 + kTile, nd);
+  for (long long p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
+    int ix, iy, iz;
+    point_coords(p, cv.st, ix, iy, iz);
+    const cpx<T> wv = h_at(cv.st, cv.vloc, cv.nl, ps, cd, ix, iy, iz, p, sigma);
+    cv.w[(long long)s * nd + p] = wv;
+    const cpx<T> pv = ps[p];
+    acc[0] += (double)pv.re * wv.re - (double)pv.im * wv.im;
+    acc[1] += (double)pv.re * wv.im + (double)pv.im * wv.re;
+  }
+  block_reduce<2>(acc, sh);
+  if (threadIdx.x == 0) {
+    double* pp = cv.part + ((long long)s * cv.tiles + blockIdx.x) * 4;
+    pp[0] = acc[0];
+    pp[1] = acc[1];
+  }
+}
+
+// x += alpha p, r -= alpha w, partials ||r||^2, r^T r
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(CocgView<T> cv) {
+  const int s = blockIdx.y;
+  if (status_of(cv.sysi, s) != kActive) return;
+  __shared__ double sh[8 * 3];
+  const long long nd = cv.nd;
+  const double* sd = cv.sysd + (long long)s * kSysD;
+  const cpx<T> al = mk<T>((T)sd[kAlpha], (T)sd[kAlpha + 1]);
+  double acc[3] = {0.0, 0.0, 0.0};
+  const long long t0 = (long long)blockIdx.x * kTile;
+  const long long t1 = min(t0 + kTile, nd);
+  for (long long p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
+    const long long q = (long long)s * nd + p;
+    const cpx<T> pv = cv.p[q], wv = cv.w[q];
+    cv.x[q] = cadd(cv.x[q], cmul(al, pv));
+    const cpx<T> rv = csub(cv.r[q], cmul(al, wv));
+    cv.r[q] = rv;
+    acc[0] += (double)rv.re * rv.re + (double)rv.im * rv.im;
+    acc[1] += (double)rv.re * rv.re - (double)rv.im * rv.im;
+    acc[2] += 2.0 * (double)rv.re * rv.im;
+  }
+  block_reduce<3>(acc, sh);
+  if (threadIdx.x == 0) {
+    double* pp = cv.part + ((long long)s * cv.tiles + blockIdx.x) * 4;
+    pp[0] = acc[0];
+    pp[2] = acc[1];
+    pp[3] = acc[2];
+  }
+}
+
+// p = r + beta p
+template <typename T>
+__global__ void __launch_bounds__(256) k_direction(CocgView<T> cv) {
+  const int s = blockIdx.y;
+  if (status_of(cv.sysi, s) != kActive) return;
+  const long long nd = cv.nd;
+  const double* sd = cv.sysd + (long long)s * kSysD;
+  const cpx<T> be = mk<T>((T)sd[kBeta], (T)sd[kBeta + 1]);
+  const long long t0 = (long long)blockIdx.x * kTile;
+  const long long t1 = min(t0 + kTile, nd);
+  for (long long p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
+    const long long q = (long long)s * nd + p;
+    cv.p[q] = cadd(cv.r[q], cmul(be, cv.p[q]));
+  }
+}
+
+// -------------------------------------------------------------------------------------------
+// per-system scalar steps (one warp per system, partial sums added in tile order)
+// -------------------------------------------------------------------------------------------
+__device__ __forceinline__ void warp_sum_tiles(const double* part, int tiles, int lane,
+                                               double (&v)[4]) {
+  for (int q = 0; q < 4; ++q) v[q] = 0.0;
+  for (int t = lane; t < tiles; t += 32)
+    for (int q = 0; q < 4; ++q) v[q] += part[(long long)t * 4 + q];
+  for (int q = 0; q < 4; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+}
+
+__device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double& qr,
+                                     double& qi) {
+  const double den = br * br + bi * bi;
+  qr = (ar * br + ai * bi) / den;
+  qi = (ai * br - ar * bi) / den;
+}
+
+// kind: 0 init after the first residual (target = tol ||b||, or round target for
+//        refinement), 1 alpha, 2 beta/convergence, 3 true-residual recheck,
+//        4 refinement check (FP64 residual of the mixed form)
+__global__ void k_scalars(int nsys, int tiles, const double* __restrict__ part, double* sysd,
+                          int* sysi, int kind, int mask, double tol, double inner_tol,
+                          int maxit, int max_restart) {
+  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= nsys) return;
+  int* si = sysi + (long long)s * kSysI;
+  double* sd = sysd + (long long)s * kSysD;
+  const int st = si[kStatus];
+  if (!((mask >> st) & 1)) return;
+  double v[4];
+  warp_sum_tiles(part + (long long)s * tiles * 4, tiles, lane, v);
+  if (lane != 0) return;
+  if (kind == 0) {  // after r0 = b - A x0
+    const double rn = sqrt(v[0]), bn = sqrt(v[1]);
+    sd[kBnorm] = bn;
+    sd[kRnorm] = rn;
+    sd[kTarget] = tol * bn;
+    sd[kRho] = v[2];
+    sd[kRho + 1] = v[3];
+    si[kIters] = 0;
+    si[kRestarts] = 0;
+    si[kStatus] = (bn == 0.0 || rn <= tol * bn) ? kFinal : kActive;
+    if (!isfinite(rn) || !isfinite(bn)) si[kStatus] = kBreakdown;
+  } else if (kind == 1) {  // alpha = rho / (p^T A p)
+    if (si[kIters] >= maxit) {
+      si[kStatus] = kMaxit;
+      return;
+    }
+    double ar, ai;
+    if ((v[0] == 0.0 && v[1] == 0.0) || !isfinite(v[0]) || !isfinite(v[1])) {
+      si[kStatus] = kBreakdown;
+      return;
+    }
+    cdiv(sd[kRho], sd[kRho + 1], v[0], v[1], ar, ai);
+    sd[kAlpha] = ar;
+    sd[kAlpha + 1] = ai;
+  } else if (kind == 2) {  // after the update: convergence test, beta
+    const double rn = sqrt(v[0]);
+    si[kIters] += 1;
+    sd[kRnorm] = rn;
+    if (!isfinite(rn)) {
+      si[kStatus] = kBreakdown;
+      return;
+    }
+    if (rn <= sd[kTarget]) {
+      si[kStatus] = kConverged;
+      return;
+    }
+    double br, bi;
+    cdiv(v[2], v[3], sd[kRho], sd[kRho + 1], br, bi);
+    sd[kBeta] = br;
+    sd[kBeta + 1] = bi;
+    sd[kRho] = v[2];
+    sd[kRho + 1] = v[3];
+  } else if (kind == 3) {  // true residual of a recursively converged system
+    const double rn = sqrt(v[0]);
+    sd[kRnormTrue] = rn;
+    if (rn <= sd[kTarget] || si[kRestarts] >= max_restart) {
+      si[kStatus] = kFinal;
+    } else {
+      si[kRestarts] += 1;
+      sd[kRho] = v[2];
+      sd[kRho + 1] = v[3];
+      si[kStatus] = (si[kIters] >= maxit) ? kMaxit : kActive;
+    }
+  } else if (kind == 4) {  // mixed form: FP64 residual of the current FP64 iterate
+    const double rn = sqrt(v[0]);
+    sd[kRnormTrue] = rn;
+    if (rn <= tol * sd[kBnorm] || !isfinite(rn)) {
+      si[kStatus] = isfinite(rn) ? kFinal : kBreakdown;
+    } else {
+      // correction round: solve A d = r in low precision from d = 0
+      sd[kTarget] = fmax(inner_tol * rn, 0.5 * tol * sd[kBnorm]);
+      sd[kRho] = v[2];
+      sd[kRho + 1] = v[3];
+      si[kStatus] = (si[kIters] >= maxit) ? kMaxit : kActive;
+      si[kRestarts] += 1;
+    }
+  } else if (kind == 5) {  // mixed form init: low-precision round 0 target
+    const double rn = sqrt(v[0]), bn = sqrt(v[1]);
+    sd[kBnorm] = bn;
+    sd[kRnorm] = rn;
+    sd[kTarget] = inner_tol * bn;
+    sd[kRho] = v[2];
+    sd[kRho + 1] = v[3];
+    si[kIters] = 0;
+    si[kRestarts] = 0;
+    si[kStatus] = (bn == 0.0 || rn <= inner_tol * bn) ? kConverged : kActive;
+    if (!isfinite(rn) || !isfinite(bn)) si[kStatus] = kBreakdown;
+  }
+}
+
+// counts of systems per status
+__global__ void k_count_status(int nsys, const int* __restrict__ sysi, int* __restrict__ counts) {
+  __shared__ int sc[kNumStatus];
+  if (threadIdx.x < kNumStatus) sc[threadIdx.x] = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < nsys; s += blockDim.x) atomicAdd(&sc[sysi[(long long)s * kSysI + kStatus]], 1);
+  __syncthreads();
+  if (threadIdx.x < kNumStatus) counts[threadIdx.x] = sc[threadIdx.x];
+}
+
+// set status for systems: active probes (lanczos flag) -> `on`, others -> kIdle
+__global__ void k_set_status(int nsys, int ns, const int* __restrict__ probe_active, int on,
+                             int* __restrict__ sysi) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  const int b = s / ns;
+  sysi[(long long)s * kSysI + kStatus] = (probe_active == nullptr || probe_active[b]) ? on : kIdle;
+}
+
+// change status from -> to
+__global__ void k_remap_status(int nsys, int from, int to, int* __restrict__ sysi) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  int* si = sysi + (long long)s * kSysI;
+  if (si[kStatus] == from) si[kStatus] = to;
+}
+
+// x64 += (double) x32 for systems whose refinement counter says they were corrected
+template <typename TH, typename TL>
+__global__ void k_accumulate(long long nd, int nsys, const int* __restrict__ sysi, int mask,
+                             int round, const cpx<TL>* __restrict__ xl, cpx<TH>* __restrict__ xh,
+                             int set) {
+  const int s = blockIdx.y;
+  if (!((mask >> sysi[(long long)s * kSysI + kStatus]) & 1)) return;
+  if (round >= 0 && sysi[(long long)s * kSysI + kRestarts] != round) return;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nd;
+       p += (long long)gridDim.x * blockDim.x) {
+    const long long q = (long long)s * nd + p;
+    const cpx<TL> a = xl[q];
+    if (set)
+      xh[q] = mk<TH>((TH)a.re, (TH)a.im);
+    else
+      xh[q] = mk<TH>(xh[q].re + (TH)a.re, xh[q].im + (TH)a.im);
+  }
+}
+
+// density response: dens_b = 4 sum_n psi_n (.) Re x_{b,n}  (Algorithm 1, inner loop)
+template <typename TX, typename TP>
+__global__ void __launch_bounds__(256) k_density(long long nd, int ns, int nb,
+                                                 const TP* __restrict__ psi,
+                                                 const cpx<TX>* __restrict__ x,
+                                                 const int* __restrict__ probe_active,
+                                                 double* __restrict__ dens) {
+  const int b = blockIdx.y;
+  if (probe_active && !probe_active[b]) return;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nd;
+       p += (long long)gridDim.x * blockDim.x) {
+    TP acc = 0;
+    for (int n = 0; n < ns; ++n)
+      acc += psi[(long long)n * nd + p] * (TP)x[((long long)b * ns + n) * nd + p].re;
+    dens[(long long)b * nd + p] = 4.0 * (double)acc;
+  }
+}
+
+// -------------------------------------------------------------------------------------------
+// launchers
+// -------------------------------------------------------------------------------------------
+template <typename T>
+cudaError_t proj_dots(const NonlocalDev<T>& nl, long long nd, int nsys, const cpx<T>* vec,
+                      const int* sysi, int mask, cpx<T>* cd, cudaStream_t st) {
+  if (nl.ngroup == 0 || nsys == 0) return cudaSuccess;
+  dim3 grid(nl.ngroup, nsys);
+  k_proj_dots<T><<<grid, 128, 0, st>>>(nl, nd, vec, sysi, mask, cd);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t apply_h(const Stencil<T>& st, const T* vloc, const NonlocalDev<T>& nl, long long nd,
+                    int count, const cpx<T>* x, const cpx<T>* sigma, cpx<T>* cd, cpx<T>* y,
+                    cudaStream_t s) {
+  cudaError_t e = proj_dots<T>(nl, nd, count, x, nullptr, 0, cd, s);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((nd + 255) / 256), count);
+  k_apply_h<T><<<grid, 256, 0, s>>>(st, vloc, nl, nd, x, sigma, cd, y);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T, typename TL>
+cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
+                       cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s) {
+  dim3 grid(cv.tiles, cv.nsys);
+  k_resid<T, TL><<<grid, 256, 0, s>>>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t cocg_iteration(const CocgView<T>& cv, double tol, int maxit, cudaStream_t s) {
+  dim3 grid(cv.tiles, cv.nsys);
+  cudaError_t e = proj_dots<T>(cv.nl, cv.nd, cv.nsys, cv.p, cv.sysi, 1 << kActive, cv.cdot, s);
+  if (e != cudaSuccess) return e;
+  k_matvec<T><<<grid, 256, 0, s>>>(cv);
+  const int sblocks = (cv.nsys + 3) / 4;
+  k_scalars<<<sblocks, 128, 0, s>>>(cv.nsys, cv.tiles, cv.part, cv.sysd, cv.sysi, 1,
+                                    1 << kActive, tol, 0.0, maxit, 0);
+  k_update<T><<<grid, 256, 0, s>>>(cv);
+  k_scalars<<<sblocks, 128, 0, s>>>(cv.nsys, cv.tiles, cv.part, cv.sysd, cv.sysi, 2,
+                                    1 << kActive, tol, 0.0, maxit, 0);
+  k_direction<T><<<grid, 256, 0, s>>>(cv);
+  note_launch(5);
+  return cudaGetLastError();
+}
+
+cudaError_t cocg_scalars(int nsys, int tiles, const double* part, double* sysd, int* sysi,
+                         int kind, int mask, double tol, double inner_tol, int maxit,
+                         int max_restart, cudaStream_t s) {
+  k_scalars<<<(nsys + 3) / 4, 128, 0, s>>>(nsys, tiles, part, sysd, sysi, kind, mask, tol,
+                                           inner_tol, maxit, max_restart);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t count_status(int nsys, const int* sysi, int* counts, cudaStream_t s) {
+  k_count_status<<<1, 1024, 0, s>>>(nsys, sysi, counts);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t set_status(int nsys, int ns, const int* probe_active, int on, int* sysi,
+                       cudaStream_t s) {
+  k_set_status<<<(nsys + 255) / 256, 256, 0, s>>>(nsys, ns, probe_active, on, sysi);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t remap_status(int nsys, int from, int to, int* sysi, cudaStream_t s) {
+  k_remap_status<<<(nsys + 255) / 256, 256, 0, s>>>(nsys, from, to, sysi);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename TH, typename TL>
+cudaError_t accumulate(long long nd, int nsys, const int* sysi, int mask, int round,
+                       const cpx<TL>* xl, cpx<TH>* xh, int set, cudaStream_t s) {
+  dim3 grid((unsigned)std::min<long long>((nd + 255) / 256, 64), nsys);
+  k_accumulate<TH, TL><<<grid, 256, 0, s>>>(nd, nsys, sysi, mask, round, xl, xh, set);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename TX, typename TP>
+cudaError_t density(long long nd, int ns, int nb, const TP* psi, const cpx<TX>* x,
+                    const int* probe_active, double* dens, cudaStream_t s) {
+  dim3 grid((unsigned)std::min<long long>((nd + 255) / 256, 256), nb);
+  k_density<TX, TP><<<grid, 256, 0, s>>>(nd, ns, nb, psi, x, probe_active, dens);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// explicit instantiations
+template cudaError_t proj_dots<double>(const NonlocalDev<double>&, long long, int,
+                                       const cpx<double>*, const int*, int, cpx<double>*,
+                                       cudaStream_t);
+template cudaError_t proj_dots<float>(const NonlocalDev<float>&, long long, int,
+                                      const cpx<float>*, const int*, int, cpx<float>*,
+                                      cudaStream_t);
+template cudaError_t apply_h<double>(const Stencil<double>&, const double*,
+                                     const NonlocalDev<double>&, long long, int,
+                                     const cpx<double>*, const cpx<double>*, cpx<double>*,
+                                     cpx<double>*, cudaStream_t);
+template cudaError_t apply_h<float>(const Stencil<float>&, const float*, const NonlocalDev<float>&,
+                                    long long, int, const cpx<float>*, const cpx<float>*,
+                                    cpx<float>*, cpx<float>*, cudaStream_t);
+template cudaError_t cocg_resid<double, double>(const CocgView<double>&, const cpx<double>*,
+                                                cpx<double>*, cpx<double>*, int, cpx<double>*,
+                                                cpx<double>*, cpx<double>*, cudaStream_t);
+template cudaError_t cocg_resid<double, float>(const CocgView<double>&, const cpx<double>*,
+                                               cpx<double>*, cpx<double>*, int, cpx<float>*,
+                                               cpx<float>*, cpx<float>*, cudaStream_t);
+template cudaError_t cocg_resid<float, float>(const CocgView<float>&, const cpx<float>*,
+                                              cpx<float>*, cpx<float>*, int, cpx<float>*,
+                                              cpx<float>*, cpx<float>*, cudaStream_t);
+template cudaError_t cocg_iteration<double>(const CocgView<double>&, double, int, cudaStream_t);
+template cudaError_t cocg_iteration<float>(const CocgView<float>&, double, int, cudaStream_t);
+template cudaError_t accumulate<double, float>(long long, int, const int*, int, int,
+                                               const cpx<float>*, cpx<double>*, int, cudaStream_t);
+template cudaError_t density<double, double>(long long, int, int, const double*,
+                                             const cpx<double>*, const int*, double*,
+                                             cudaStream_t);
+template cudaError_t density<float, float>(long long, int, int, const float*, const cpx<float>*,
+                                           const int*, double*, cudaStream_t);
+template cudaError_t density<double, float>(long long, int, int, const float*,
+                                            const cpx<double>*, const int*, double*,
+                                            cudaStream_t);
+
+}  // namespace rpa

@@ -1,0 +1,92 @@
+// Batched COCG for the Sternheimer systems: shared declarations.
+#pragma once
+#include <algorithm>
+
+#include "rpa_internal.cuh"
+
+namespace rpa {
+
+constexpr int kTile = 1024;  // grid points per block in the COCG kernels
+
+// per-system scalar layout (doubles)
+constexpr int kSysD = 16;
+constexpr int kRho = 0, kAlpha = 2, kBeta = 4, kBnorm = 6, kTarget = 7, kRnorm = 8,
+              kRnormTrue = 9;
+// per-system ints
+constexpr int kSysI = 4;
+constexpr int kStatus = 0, kIters = 1, kRestarts = 2;
+// statuses
+constexpr int kActive = 0, kConverged = 1, kFinal = 2, kMaxit = 3, kBreakdown = 4, kIdle = 5;
+constexpr int kNumStatus = 6;
+
+template <typename T>
+struct CocgView {
+  Stencil<T> st;
+  const T* vloc;
+  NonlocalDev<T> nl;
+  long long nd;
+  int nsys, ns, tiles;
+  const T* psi;          // ns x N_d
+  const double* eps;     // ns
+  const double* omega;   // per probe slot
+  const T* u;            // per probe slot, N_d
+  cpx<T>*x, *r, *p, *w;  // nsys x N_d
+  cpx<T>* cdot;          // nsys x ngroup x 4
+  double* part;          // nsys x tiles x 4
+  double* sysd;          // nsys x kSysD
+  int* sysi;             // nsys x kSysI
+};
+
+template <typename T>
+cudaError_t proj_dots(const NonlocalDev<T>& nl, long long nd, int nsys, const cpx<T>* vec,
+                      const int* sysi, int mask, cpx<T>* cd, cudaStream_t st);
+template <typename T>
+cudaError_t apply_h(const Stencil<T>& st, const T* vloc, const NonlocalDev<T>& nl, long long nd,
+                    int count, const cpx<T>* x, const cpx<T>* sigma, cpx<T>* cd, cpx<T>* y,
+                    cudaStream_t s);
+template <typename T, typename TL>
+cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
+                       cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s);
+template <typename T>
+cudaError_t cocg_iteration(const CocgView<T>& cv, double tol, int maxit, cudaStream_t s);
+cudaError_t cocg_scalars(int nsys, int tiles, const double* part, double* sysd, int* sysi,
+                         int kind, int mask, double tol, double inner_tol, int maxit,
+                         int max_restart, cudaStream_t s);
+cudaError_t count_status(int nsys, const int* sysi, int* counts, cudaStream_t s);
+cudaError_t set_status(int nsys, int ns, const int* probe_active, int on, int* sysi,
+                       cudaStream_t s);
+cudaError_t remap_status(int nsys, int from, int to, int* sysi, cudaStream_t s);
+template <typename TH, typename TL>
+cudaError_t accumulate(long long nd, int nsys, const int* sysi, int mask, int round,
+                       const cpx<TL>* xl, cpx<TH>* xh, int set, cudaStream_t s);
+template <typename TX, typename TP>
+cudaError_t density(long long nd, int ns, int nb, const TP* psi, const cpx<TX>* x,
+                    const int* probe_active, double* dens, cudaStream_t s);
+
+// dense.cu ----------------------------------------------------------------------------------
+// Galerkin projection over the occupied space (Section 4):
+//   G_b = -dV Psi diag(u_b) Psi^T  (N_s x N_s per probe slot b),
+//   C_b[k][n] = G_b[k][n] / (eps_k - eps_n - i w_b),
+//   x0_{b,n} = sum_k psi_k C_b[k][n].
+template <typename T>
+cudaError_t galerkin_guess(long long nd, int ns, int nb, const T* psi, const double* eps,
+                           const double* omega, const T* u, const int* probe_active, double dV,
+                           double* gpart, int nchunk, cpx<T>* cmat, cpx<T>* x0, cudaStream_t s);
+// Mode products along one axis of a batch of 3-D arrays: out[..a..] = sum_i Mt[i][a] in[..i..]
+// (Mt is nin x nout, row-major).  dims_in = (nx, ny, nz) of the input; batch strides in_bs and
+// out_bs.  Optional elementwise scale of the output (same layout as the output).
+template <typename TI, typename TO, typename T>
+cudaError_t mode_product(const TI* in, long long in_bs, TO* out, long long out_bs, const T* Mt,
+                         int axis, const int* dims_in, int nout, int batch, const T* scale,
+                         cudaStream_t s);
+// Lanczos helpers (FP64): dots, combination, norm, normalisation
+cudaError_t multi_dot(long long nd, int nb, const double* Q, long long ldq, int m0, int m1,
+                      const double* v, const int* active, double* part, int nchunk,
+                      double* dots, cudaStream_t s);
+cudaError_t multi_axpy(long long nd, int nb, const double* Q, long long ldq, int m0, int m1,
+                       const double* coef, int ldc, double* v, const int* active, cudaStream_t s);
+cudaError_t convert_d2f(const double* a, float* b, long long n, cudaStream_t s);
+cudaError_t convert_f2d(const float* a, double* b, long long n, cudaStream_t s);
+cudaError_t jacobi_eig(double* a, double* v, double* lam, int n, cudaStream_t s);
+
+}  // namespace rpa
