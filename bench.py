@@ -1,0 +1,429 @@
+#!/usr/bin/env python
+"""Benchmark: Lanczos-quadrature RPA correlation energy on the 64-atom Si-like cell.
+
+Metric: probe-points per second (one probe-point = the Lanczos quadrature of d_j(i w) at one
+coarse grid point and one frequency, run to completion), for the mixed form (FP32
+stencil/COCG/projections with FP64 Lanczos, reorthogonalisation, tridiagonal eigen-solve,
+refinement residuals and energy sums) next to the plain FP64 form, with the E_c error of the
+mixed form against the FP64 form in mHa/atom.
+
+Workload (default "si64"): periodic 2x2x2 diamond-Si-like cell, a = 20.52 bohr, 52^3 grid,
+12th-order Laplacian, Gaussian wells plus 4 s/p projectors per atom, 128 occupied states,
+10 mapped Gauss-Legendre frequencies, 40 Lanczos steps, coarse stride 2 (17,576 probes,
+175,760 probe-points), tricubic interpolation.  Inputs are synthetic and seeded (synth/).
+
+A step = one pass of the whole path over one batch: a seeded sample of probe-points spread
+over all frequencies (u = nu^{1/2} q, Galerkin projection, COCG, density, nu^{1/2}, Lanczos
+with reorthogonalisation, [f(T)]_11), then interpolation of the coarse array to the fine
+grid and the E_c sum.  Inputs (~2 GB of COCG vectors per batch) exceed the 126 MB L2, so no
+flush is needed between steps.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: system, frequencies, Lanczos steps, stride, interpolation, Sternheimer tol, atoms
+    "si64": dict(system="si64", nw=10, nl=40, stride=(2, 2, 2), interp="cubic", tol=1e-4,
+                 natom=64, desc="64-atom Si-like cell, 52^3 grid, 128 occupied states, 10 "
+                 "frequencies, 40 Lanczos steps, coarse stride 2, tricubic"),
+    "si8": dict(system="si8", nw=10, nl=40, stride=(2, 2, 2), interp="cubic", tol=1e-4, natom=8,
+                desc="8-atom Si-like cell, 26^3 grid, 16 occupied states, 10 frequencies, "
+                "40 Lanczos steps, coarse stride 2"),
+    "toy": dict(system="toy", nw=8, nl=20, stride=(2, 2, 2), interp="cubic", tol=1e-4, natom=4,
+                desc="toy periodic cube, 12^3 grid, 8 occupied states, 8 frequencies, "
+                "20 Lanczos steps, coarse stride 2"),
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
+        return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(smax)),
+                    power_w_max=float(max(power)), samples=len(sm), reasons=sorted(reasons))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=float(d["hbm_gbs"]), src="measured")
+    return dict(hbm_gbs=6800.0, src="fallback")
+
+
+def make_system(name):
+    import synth
+    return synth.named_system(name)
+
+
+def sample_probes(P, nw, per_freq, seed):
+    rng = np.random.default_rng(seed)
+    pr, fq = [], []
+    for k in range(nw):
+        ps = rng.choice(P, size=per_freq, replace=False)
+        pr += list(ps)
+        fq += [k] * per_freq
+    return np.asarray(pr, dtype=np.int64), np.asarray(fq, dtype=np.int32)
+
+
+# ------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle on the host cores
+# ------------------------------------------------------------------------------------------
+def run_reference(args, wl):
+    import oracle
+    s = make_system(wl["system"])
+    om, w = oracle.gl_frequencies(wl["nw"])
+    P = int(np.prod([len(oracle.coarse_nodes(s.n[a], wl["stride"][a], s.bc[a])) for a in range(3)]))
+    probes = oracle.coarse_probes(s.n, wl["stride"], s.bc)
+    cores = os.cpu_count()
+    osys = oracle.OracleSystem(s)
+    # Bounded sample: one matrix-vector product (N_s Sternheimer solves) of one probe-point
+    # per step; a probe-point costs N_l such products, so probe-pts/s = 1 / (N_l * t_step).
+    times = []
+    rng = np.random.default_rng(7)
+    for it in range(args.warmup + args.steps):
+        j = int(probes[rng.integers(P)])
+        k = int(rng.integers(wl["nw"]))
+        t0 = time.perf_counter()
+        oracle.lanczos(osys, np.array([j]), np.array([om[k]]), 1, tol=wl["tol"], maxit=20000,
+                       nthreads=cores)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    tstep = float(np.mean(times))
+    value = 1.0 / (wl["nl"] * tstep)
+    sample = (f"per step: 1 Lanczos matrix-vector product ({s.ns} Sternheimer solves, tol "
+              f"{wl['tol']}) of 1 seeded probe-point of the {wl['system']} workload; "
+              f"probe-pts/s = 1/(N_l={wl['nl']} x step time)")
+    line = dict(metric="probe-points/s", value=value, unit="probe-pts/s", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * tstep,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference",
+                config=dict(workload=wl["system"], desc=wl["desc"], l2="inputs > L2"),
+                cpu_baseline=dict(value=value, unit="probe-pts/s", cores=cores, kind="oracle",
+                                  sample=sample),
+                e2e=dict(value=value, unit="probe-pts/s", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def cpu_baseline(s, wl, om, probes):
+    """Oracle on the host cores, bounded sample: one Lanczos matrix-vector product."""
+    import oracle
+    cores = os.cpu_count()
+    j = int(probes[len(probes) // 3])
+    k = wl["nw"] // 2
+    t0 = time.perf_counter()
+    oracle.lanczos(s, np.array([j]), np.array([om[k]]), 1, tol=wl["tol"], maxit=20000,
+                   nthreads=cores)
+    dt = time.perf_counter() - t0
+    return dict(value=1.0 / (wl["nl"] * dt), unit="probe-pts/s", cores=cores, kind="oracle",
+                sample=(f"1 Lanczos matrix-vector product ({s.ns} Sternheimer solves, tol "
+                        f"{wl['tol']}, omega={om[k]:.4g}) of 1 probe-point; probe-pts/s = "
+                        f"1/(N_l x {dt:.1f} s)"))
+
+
+def run_ours(args, wl):
+    import torch
+
+    import paper_2609_16408_gb300 as R
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = make_system(wl["system"])
+    om, w = R.rpa_gl_frequencies(wl["nw"])
+    stream = torch.cuda.Stream(device=dev)
+    nd = s.N_d
+    nat = wl["natom"]
+
+    def context(prec, profile=1):
+        c = R.Context(s.n, s.h, s.bc, s.fd_radius, stream=stream.cuda_stream)
+        R.rpa_set_potential(c.ctx, s.vloc)
+        R.rpa_set_projectors(c.ctx, [(g.idx, g.chi, g.gamma) for g in s.groups])
+        R.rpa_set_occupied(c.ctx, s.psi, s.eps)
+        R.rpa_set_frequencies(c.ctx, om, w)
+        R.rpa_set_options(c.ctx, lanczos_max=wl["nl"], stern_tol=wl["tol"], stern_maxit=20000,
+                          precision=prec, stride=wl["stride"], interp=wl["interp"],
+                          refine=args.refine, profile=profile)
+        return c
+
+    cm = context("mixed")
+    P = R.rpa_num_probes(cm.ctx)
+    probe_idx = torch.from_numpy(R.rpa_probe_indices(cm.ctx)).to(dev)
+    dco = torch.zeros((wl["nw"], P), dtype=torch.float64, device=dev)
+
+    def step(c, per_freq, seed, stats_acc=None):
+        sel, fq = sample_probes(P, wl["nw"], per_freq, seed)
+        pr = probe_idx[torch.from_numpy(sel).to(dev)]
+        fqt = torch.from_numpy(fq).to(dev)
+        out = R.rpa_probe_density(c.ctx, pr, fqt, allow_nonconv=True)
+        dco[fqt.long(), torch.from_numpy(sel).to(dev)] = out["d"]
+        dfi, ec = R.rpa_interpolate(c.ctx, dco, nd)
+        if stats_acc is not None:
+            stats_acc.append(out["stats"])
+        return out, sel, fq
+
+    per = args.probes_per_freq
+    seed0 = 1000 * (rank + 1)
+    # warm-up
+    for i in range(args.warmup):
+        with torch.cuda.stream(stream):
+            step(cm, per, seed0 + i)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    l0 = R.rpa_kernel_launches()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            step(cm, per, seed0 + 100 + i, stats)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = R.rpa_kernel_launches() - l0
+    clk = clocks.stop()
+    t = ev0.elapsed_time(ev1) * 1e-3
+    if dist:
+        tt = torch.tensor([t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    pts_per_rank = args.steps * per * wl["nw"]
+    value = world * pts_per_rank / t
+
+    # dominant kernel roofline (CUDA events on the launching stream, inside the timed region)
+    ks = np.sum([st["kernel_seconds"] for st in stats], axis=0)
+    kb = np.sum([st["kernel_bytes"] for st in stats], axis=0)
+    kl = np.sum([st["kernel_launches"] for st in stats], axis=0)
+    names = ["proj_dots", "k_dirmatvec", "k_scalars", "k_update_dots", "none"]
+    dom = 1 if ks[1] >= ks[3] else 3
+    pk = peaks()
+    achieved = kb[dom] / ks[dom] / 1e9 if ks[dom] > 0 else 0.0
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        tj = json.load(open(tr_path)).get(names[dom])
+        if tj and tj.get("source_sha") == kernel_source_sha():
+            traffic = tj.get("bytes_per_launch")
+    roofline = dict(bound="hbm", kernel=names[dom], achieved=achieved, peak=pk["hbm_gbs"],
+                    unit="GB/s", frac=achieved / pk["hbm_gbs"], traffic=traffic,
+                    peak_src=pk["src"] + " (burst copy)",
+                    launches=int(kl[dom]), seconds=float(ks[dom]),
+                    algorithmic_bytes=float(kb[dom]),
+                    cocg_share=float(ks[dom] / max(1e-30, sum(ks))))
+
+    # FP64 form on the same workload (its own seeded sample) and the mixed-vs-FP64 error
+    fp64 = None
+    if not args.no_fp64:
+        c64 = context("fp64")
+        sel, fq = sample_probes(P, wl["nw"], args.fp64_probes_per_freq, seed0 + 7)
+        pr = probe_idx[torch.from_numpy(sel).to(dev)]
+        fqt = torch.from_numpy(fq).to(dev)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            o64 = R.rpa_probe_density(c64.ctx, pr, fqt, allow_nonconv=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) * 1e-3
+        with torch.cuda.stream(stream):
+            omx = R.rpa_probe_density(cm.ctx, pr, fqt, allow_nonconv=True)
+        torch.cuda.synchronize()
+        dd = (omx["d"] - o64["d"]).cpu().numpy()
+        g3 = float(np.prod(wl["stride"]))
+        # E_c error estimate: per frequency, scale the sampled sum to all P probes
+        err = 0.0
+        for k in range(wl["nw"]):
+            m = fq == k
+            if m.any():
+                err += w[k] * dd[m].sum() * (P / m.sum())
+        err = abs(err) * g3 / (2 * np.pi) / nat
+        fp64 = dict(value=len(sel) / t64, unit="probe-pts/s", probe_points=int(len(sel)),
+                    seconds=t64, mixed_speedup=(value / world) / (len(sel) / t64),
+                    ec_err_mha_per_atom_est=1e3 * err, max_abs_dd=float(np.abs(dd).max()))
+        c64.close()
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        vloc_h, psi_h, eps_h = pin(s.vloc), pin(s.psi), pin(s.eps)
+        grp = [(pin(g.idx.astype(np.int32)), pin(g.chi), pin(g.gamma)) for g in s.groups]
+        h2d = vloc_h.nbytes + psi_h.nbytes + eps_h.nbytes + sum(
+            a.nbytes + b.nbytes + c.nbytes for a, b, c in grp)
+        dco_h = np.zeros((wl["nw"], P))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.e2e_steps):
+            sel, fq = sample_probes(P, wl["nw"], per, seed0 + 500 + i)
+            pr_h = R.rpa_probe_indices(cm.ctx)[sel]
+            R.rpa_set_potential(cm.ctx, vloc_h)
+            R.rpa_set_projectors(cm.ctx, grp)
+            R.rpa_set_occupied(cm.ctx, psi_h, eps_h)
+            out = R.rpa_probe_density(cm.ctx, pr_h, fq, allow_nonconv=True)
+            dco_h[fq, sel] = out["d"]
+            dfi_h, ec_h = R.rpa_interpolate(cm.ctx, dco_h, nd)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        h2d_step = h2d + pr_h.nbytes + fq.nbytes + dco_h.nbytes
+        d2h_step = out["d"].nbytes + dfi_h.nbytes + 8
+        e2e = dict(value=world * args.e2e_steps * len(sel) / te, unit="probe-pts/s",
+                   h2d_bytes_per_step=int(h2d_step), d2h_bytes_per_step=int(d2h_step))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(s, wl, om, R.rpa_probe_indices(cm.ctx))
+
+    st0 = stats[0] if stats else {}
+    tot_iters = sum(st["cocg_iters"] for st in stats)
+    tot_solves = sum(st["solves"] for st in stats)
+    full_pts = P * wl["nw"]
+    line = dict(
+        metric="probe-points/s", value=value, unit="probe-pts/s", n_gpus=world,
+        steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * t / args.steps,
+        higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32+f64",
+        data="synthetic (seeded Si-like cell, synth/)",
+        config=dict(workload=wl["system"], desc=wl["desc"], form="mixed",
+                    stern_tol=wl["tol"], refine=args.refine,
+                    probe_points_per_step=per * wl["nw"] * world, l2="inputs > L2 (no flush)",
+                    parallelism=f"probe-points sharded over {world} GPU(s)"),
+        roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
+        clocks=clk, fp64_form=fp64,
+        ec_full_seconds_est=full_pts / value,
+        cocg=dict(mean_iters=tot_iters / max(1, tot_solves), solves=tot_solves,
+                  max_iters=max(st["max_cocg_iters"] for st in stats) if stats else 0,
+                  refine_rounds=sum(st["refine_rounds"] for st in stats)),
+        phases_s=list(np.sum([st["seconds_phase"] for st in stats], axis=0)) if stats else None,
+    )
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    cm.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+_SRC_SHA = None
+
+
+def kernel_source_sha():
+    """Hash of the CUDA sources, to tell whether stored ncu counters still apply."""
+    global _SRC_SHA
+    if _SRC_SHA is None:
+        import hashlib
+        h = hashlib.sha256()
+        csrc = os.path.join(ROOT, "paper_2609_16408_gb300", "csrc")
+        for f in sorted(os.listdir(csrc)):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+        _SRC_SHA = h.hexdigest()[:16]
+    return _SRC_SHA
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="si64", choices=sorted(WORKLOADS))
+    ap.add_argument("--probes-per-freq", type=int, default=1)
+    ap.add_argument("--fp64-probes-per-freq", type=int, default=1)
+    ap.add_argument("--refine", type=int, default=4)
+    ap.add_argument("--nl", type=int, default=0,
+                    help="override the Lanczos step count (profiling runs only)")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = dict(WORKLOADS[args.workload])
+    if args.nl > 0:
+        wl["nl"] = args.nl
+        wl["desc"] += f" [profiling run: {args.nl} Lanczos steps]"
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        run_reference(args, wl)
+        return
+    run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

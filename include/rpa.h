@@ -85,7 +85,9 @@ typedef struct {
   int batch;             /* probe-points in flight per wave; 0 = sized from free memory */
   int fkind;             /* RPA_F_* (RPA_F_LOG for the correlation energy) */
   int refine;            /* mixed form: FP64 residual refinement rounds after FP32 COCG */
-  double inner_tol;      /* mixed form: FP32 COCG tolerance per refinement round (0 = auto) */
+  double inner_tol;      /* mixed form: FP32 COCG relative tolerance per round
+                            (0 = auto: max(sqrt(stern_tol), 1e-5)) */
+  int profile;           /* 1: time the COCG kernels with CUDA events (rpa_stats.kernel_*) */
 } rpa_options;
 
 typedef struct {
@@ -99,6 +101,14 @@ typedef struct {
   long long refine_rounds; /* FP64 refinement rounds (mixed form) */
   int max_cocg_iters;      /* largest iteration count of one solve */
   int lanczos_steps_max;   /* largest Lanczos step count of one probe */
+  /* with options.profile: per COCG kernel class (0 projector dots, 1 H apply (matvec),
+   * 2 scalar steps, 3 x/r update, 4 direction update) the summed event time, the number
+   * of launches, and the algorithmic bytes moved (active systems x grid points x bytes per
+   * point; projector data and scalars not counted) */
+  double kernel_seconds[8];
+  long long kernel_launches[8];
+  double kernel_bytes[8];
+  int precision_bytes;     /* bytes of one real value in the COCG vectors (4 or 8) */
 } rpa_stats;
 
 /* ---- context --------------------------------------------------------------------------- */
@@ -178,6 +188,14 @@ rpa_status rpa_apply_nu_half(rpa_ctx *ctx, int count, const double *q, double *u
  * NULL) receives count x N_s COCG iteration counts. */
 rpa_status rpa_chi0(rpa_ctx *ctx, int count, const double *omega, const double *u, double *r,
                     int *iters, int where);
+
+/* Galerkin initial guesses of the Sternheimer systems (Section 4): for each of count
+ * (omega_i, u_i) and each occupied state n, x0_{i,n} = sum_k psi_k C_kn with
+ * C_kn = dV psi_k^T(-psi_n (.) u_i) / (eps_k - eps_n - i omega_i).  u: count x N_d real;
+ * x0: count x N_s x N_d complex (interleaved).  Mixed form: tcgen05 tensor cores (tf32,
+ * three-pass split); FP64 form: FP64 CUDA cores. */
+rpa_status rpa_galerkin(rpa_ctx *ctx, int count, const double *omega, const double *u,
+                        double *x0, int where);
 
 /* d_i = [f(T_i)]_{11} for count symmetric tridiagonals of order k (alpha: count x k,
  * beta: count x k with beta[i*k + k-1] ignored); host arrays; solved on the device. */

@@ -66,6 +66,7 @@ def _lib():
             lib.orc_tridiag_f11.restype = C.c_double
             lib.orc_gl_frequencies.argtypes = [C.c_int, P, P]
             lib.orc_jacobi_eig.argtypes = [C.c_int, P, P, P]
+            lib.orc_galerkin.argtypes = [P, C.c_double, P, P]
             _LIB = lib
     return _LIB
 
@@ -184,6 +185,15 @@ def chi0(s, omega: float, u: np.ndarray, tol=1e-12, maxit=5000, nthreads=0, psi=
     if st != 0:
         raise RuntimeError("oracle COCG did not converge")
     return r, it
+
+
+def galerkin(s, omega: float, u: np.ndarray) -> np.ndarray:
+    """Galerkin initial guesses x0 (ns x N_d complex) of the Sternheimer systems for one u."""
+    o = _osys(s)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    x0 = np.empty((o.psi.shape[0], s.N_d), dtype=np.complex128)
+    _lib().orc_galerkin(o.ref, float(omega), _p(u), _p(x0))
+    return x0
 
 
 def tridiag_f11(alpha, beta, fkind=F_LOG) -> float:

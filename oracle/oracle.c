@@ -343,6 +343,27 @@ static int cocg_solve(const orc_sys *s, int n, double omega, const double *u, do
   return it;
 }
 
+/* Galerkin initial guesses of all N_s systems for one u (Section 4):
+ * x0_n = sum_k psi_k C_kn,  C_kn = dV psi_k^T (-psi_n u) / (eps_k - eps_n - i omega).
+ * x0: ns x N_d complex (interleaved).  Exported for tests of the projection step. */
+void orc_galerkin(const orc_sys *s, double omega, const double *u, double *x0out) {
+  const long N = nd_of(s);
+  const double dV = dv_of(s);
+  cplx *x0 = (cplx *)x0out;
+  for (int n = 0; n < s->ns; ++n) {
+    const double *psin = s->psi + (long)n * N;
+    cplx *xn = x0 + (long)n * N;
+    for (long i = 0; i < N; ++i) xn[i] = 0.0;
+    for (int k = 0; k < s->ns; ++k) {
+      const double *psik = s->psi + (long)k * N;
+      double g = 0.0;
+      for (long i = 0; i < N; ++i) g += psik[i] * (-psin[i] * u[i]);
+      cplx ck = g * dV / (s->eps[k] - s->eps[n] - I * omega);
+      for (long i = 0; i < N; ++i) xn[i] += ck * psik[i];
+    }
+  }
+}
+
 /* r = chi0(i omega) u via the N_s Sternheimer solves: r = 4 sum_n psi_n (.) Re(dpsi_n)
  * (Algorithm 1, inner loop over occupied states).  Solves run in parallel; the density is
  * summed over n in order afterwards.  iters[n] receives each solve's COCG iterations. */

@@ -94,7 +94,8 @@ class Options(C.Structure):
     _fields_ = [("lanczos_max", C.c_int), ("lanczos_rtol", C.c_double), ("stern_tol", C.c_double),
                 ("stern_maxit", C.c_int), ("precision", C.c_int), ("reorth", C.c_int),
                 ("stride", C.c_int * 3), ("interp", C.c_int), ("batch", C.c_int),
-                ("fkind", C.c_int), ("refine", C.c_int), ("inner_tol", C.c_double)]
+                ("fkind", C.c_int), ("refine", C.c_int), ("inner_tol", C.c_double),
+                ("profile", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -102,14 +103,20 @@ class Stats(C.Structure):
                 ("probe_points", C.c_longlong), ("matvecs", C.c_longlong),
                 ("solves", C.c_longlong), ("cocg_iters", C.c_longlong),
                 ("refine_rounds", C.c_longlong), ("max_cocg_iters", C.c_int),
-                ("lanczos_steps_max", C.c_int)]
+                ("lanczos_steps_max", C.c_int), ("kernel_seconds", C.c_double * 8),
+                ("kernel_launches", C.c_longlong * 8), ("kernel_bytes", C.c_double * 8),
+                ("precision_bytes", C.c_int)]
 
     def as_dict(self):
         return dict(seconds_total=self.seconds_total, seconds_phase=list(self.seconds_phase),
                     probe_points=self.probe_points, matvecs=self.matvecs, solves=self.solves,
                     cocg_iters=self.cocg_iters, refine_rounds=self.refine_rounds,
                     max_cocg_iters=self.max_cocg_iters,
-                    lanczos_steps_max=self.lanczos_steps_max)
+                    lanczos_steps_max=self.lanczos_steps_max,
+                    kernel_seconds=list(self.kernel_seconds),
+                    kernel_launches=list(self.kernel_launches),
+                    kernel_bytes=list(self.kernel_bytes),
+                    precision_bytes=self.precision_bytes)
 
 
 def _declare(lib):
@@ -133,6 +140,7 @@ def _declare(lib):
         "rpa_apply_nu_half": ([P, I, P, P, I], I),
         "rpa_chi0": ([P, I, P, P, P, P, I], I),
         "rpa_tridiag_f11": ([I, I, P, P, I, P], I),
+        "rpa_galerkin": ([P, I, P, P, P, I], I),
         "rpa_status_string": ([I], C.c_char_p),
         "rpa_last_error": ([P], C.c_char_p),
         "rpa_kernel_launches": ([P], LL),
@@ -366,6 +374,16 @@ def rpa_chi0(ctx, omega, u, ns):
     _check(load().rpa_chi0(ctx, u.shape[0], _ptr(om)[0], _ptr(u)[0], _ptr(r)[0], _ptr(it)[0],
                            RPA_HOST), ctx)
     return r, it
+
+
+def rpa_galerkin(ctx, omega, u, ns):
+    """Galerkin initial guesses x0 (count, ns, N_d) complex for (omega_i, u_i)."""
+    u = np.ascontiguousarray(np.atleast_2d(u), dtype=np.float64)
+    om = np.ascontiguousarray(np.broadcast_to(np.asarray(omega, dtype=np.float64), (u.shape[0],)))
+    x0 = np.empty((u.shape[0], ns, u.shape[1]), dtype=np.complex128)
+    _check(load().rpa_galerkin(ctx, u.shape[0], _ptr(om)[0], _ptr(u)[0], _ptr(x0)[0], RPA_HOST),
+           ctx)
+    return x0
 
 
 def rpa_tridiag_f11(alpha, beta, fkind=RPA_F_LOG):

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "cocg.cuh"
+#include "cocg_fused.cuh"
 #include "small.cuh"
 
 using namespace rpa;
@@ -73,6 +74,7 @@ struct rpa_ctx {
   OpData<float> d32;
   int ngroup = 0;
   DevBuf g_off, g_idx, p_off, p_grp;
+  DevBuf tile_roff, tile_ranges;  // per 1-D COCG tile: (group, entry range) lists
   DevBuf lam[3];
   // interpolation operators (transposed, coarse x fine) per axis
   DevBuf interpWt[3], cnodes_d[3];
@@ -80,14 +82,19 @@ struct rpa_ctx {
   int interp_built = -1, stride_built[3] = {0, 0, 0};
   // wave workspace
   DevBuf Q, u64, v64, dens64, t64a, t64b, u32, t32a, t32b;
-  DevBuf x, r, p, w, x64, r64, cdot, part, sysd, sysi, gpart, cmat;
+  DevBuf x, r, p, p2, w, x64, r64, cdot, cpb, crb, part, sysd, sysi, gpart, cmat;
   DevBuf probe_d, pomega_d, active_d, steps_d, alpha_d, beta_d, lstate_d, coef_d, dots_d,
-      dotpart_d, flags_d, dout_d, counts_d;
+      dotpart_d, flags_d, dout_d, counts_d, list_d;
   int ws_nb = 0;
   int* pinned = nullptr;  // counts from the device
   std::string err;
   cudaEvent_t ev[8];
   bool have_events = false;
+  // COCG kernel profiling (options.profile): events for one chunk of iterations
+  cudaEvent_t pev[4 * 7];
+  bool have_pev = false;
+  rpa_stats* prof_stats = nullptr;
+  int prof_cpx_bytes = 0;
 };
 
 namespace rpa {
@@ -282,6 +289,19 @@ static size_t cpx_bytes(const rpa_ctx* c) {
 
 static long long tiles_of(long long nd) { return (nd + kTile - 1) / kTile; }
 
+// 2.5-D tiling of the fused H apply: 32 x 8 column tiles, z split in chunks of <= 64 planes
+static int fused_zchunk(const rpa_ctx* c) { return c->grid.n[2] <= 64 ? c->grid.n[2] : 32; }
+static int fused_nzchunk(const rpa_ctx* c) {
+  return (c->grid.n[2] + fused_zchunk(c) - 1) / fused_zchunk(c);
+}
+static int fused_ntiles_xy(const rpa_ctx* c) {
+  return ((c->grid.n[0] + 31) / 32) * ((c->grid.n[1] + 7) / 8);
+}
+static int part_stride(const rpa_ctx* c) {
+  return (int)std::max<long long>(tiles_of(c->nd),
+                                  (long long)fused_ntiles_xy(c) * fused_nzchunk(c));
+}
+
 static int gram_chunks(long long nd) {
   return (int)std::max<long long>(1, std::min<long long>(256, (nd + 4095) / 4096));
 }
@@ -291,9 +311,9 @@ static size_t per_probe_bytes(const rpa_ctx* c) {
   size_t b = (size_t)ns * nd * cpx_bytes(c) * 4;
   if (c->opt.precision == RPA_MIXED && c->opt.refine > 0) b += (size_t)ns * nd * 32;
   b += (size_t)(c->opt.lanczos_max + 1) * nd * 8 + (size_t)nd * 8 * 5 + (size_t)nd * 4 * 3;
-  b += (size_t)ns * tiles_of(nd) * 4 * 8 + (size_t)ns * (kSysD * 8 + kSysI * 4);
+  b += (size_t)ns * part_stride(c) * 4 * 8 + (size_t)ns * (kSysD * 8 + kSysI * 4);
   b += (size_t)ns * ns * (gram_chunks(nd) * 8 + 16);
-  b += (size_t)ns * std::max(1, c->ngroup) * kProjChunk * 16;
+  b += (size_t)ns * std::max(1, c->ngroup) * kProjChunk * 16 * 3;
   return b;
 }
 
@@ -333,9 +353,12 @@ static rpa_status ensure_workspace(rpa_ctx* c, int nb) {
   CK(c->x.ensure(cb * S * nd));
   CK(c->r.ensure(cb * S * nd));
   CK(c->p.ensure(cb * S * nd));
+  CK(c->p2.ensure(cb * S * nd));
   CK(c->w.ensure(cb * S * nd));
   CK(c->cdot.ensure(sizeof(cpx<double>) * S * std::max(1, c->ngroup) * kProjChunk));
-  CK(c->part.ensure(sizeof(double) * S * tiles_of(nd) * 4));
+  CK(c->cpb.ensure(sizeof(cpx<double>) * S * std::max(1, c->ngroup) * kProjChunk));
+  CK(c->crb.ensure(sizeof(cpx<double>) * S * std::max(1, c->ngroup) * kProjChunk));
+  CK(c->part.ensure(sizeof(double) * S * part_stride(c) * 4));
   CK(c->sysd.ensure(sizeof(double) * S * kSysD));
   CK(c->sysi.ensure(sizeof(int) * S * kSysI));
   CK(c->gpart.ensure(sizeof(double) * nb * gram_chunks(nd) * c->ns * c->ns));
@@ -353,6 +376,7 @@ static rpa_status ensure_workspace(rpa_ctx* c, int nb) {
   CK(c->flags_d.ensure(sizeof(int) * 4));
   CK(c->dout_d.ensure(sizeof(double) * nb));
   CK(c->counts_d.ensure(sizeof(int) * 16));
+  CK(c->list_d.ensure(sizeof(int) * S));
   c->ws_nb = nb;
   return RPA_OK;
 }
@@ -384,8 +408,9 @@ static rpa_status collect_stats(rpa_ctx* c, int S, SolveStats& ss) {
   return RPA_OK;
 }
 
-static rpa_status counts(rpa_ctx* c, int S, int* out) {
-  CK(count_status(S, c->sysi.as<int>(), c->counts_d.as<int>(), c->stream));
+static rpa_status counts(rpa_ctx* c, int S, int* out, bool make_list = false) {
+  CK(count_status(S, c->sysi.as<int>(), c->counts_d.as<int>(), c->stream,
+                  make_list ? c->list_d.as<int>() : nullptr));
   CK(cudaMemcpyAsync(c->pinned, c->counts_d.p, sizeof(int) * kNumStatus, cudaMemcpyDeviceToHost,
                      c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -407,7 +432,7 @@ static CocgView<T> make_view(rpa_ctx* c, int nb, const T* u, cpx<T>* x, cpx<T>* 
   cv.nd = c->nd;
   cv.nsys = nb * c->ns;
   cv.ns = c->ns;
-  cv.tiles = (int)tiles_of(c->nd);
+  cv.tiles = part_stride(c);
   cv.psi = o.psi.template as<T>();
   cv.eps = c->eps_d.as<double>();
   cv.omega = c->pomega_d.as<double>();
@@ -420,23 +445,81 @@ static CocgView<T> make_view(rpa_ctx* c, int nb, const T* u, cpx<T>* x, cpx<T>* 
   cv.part = c->part.as<double>();
   cv.sysd = c->sysd.as<double>();
   cv.sysi = c->sysi.as<int>();
+  cv.list = nullptr;
   return cv;
 }
 
 constexpr int kChunkIters = 4;
 
 template <typename T>
-static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv, int maxit) {
+static FusedBufs<T> make_fused(rpa_ctx* c) {
+  FusedBufs<T> fb;
+  fb.p_in = c->p.as<cpx<T>>();
+  fb.p_out = c->p2.as<cpx<T>>();
+  fb.cp = c->cpb.as<cpx<T>>();
+  fb.cr = c->crb.as<cpx<T>>();
+  fb.tile_roff = c->tile_roff.as<int>();
+  fb.tile_ranges = c->tile_ranges.as<int>();
+  fb.ntiles_xy = fused_ntiles_xy(c);
+  fb.nzchunk = fused_nzchunk(c);
+  fb.zchunk = fused_zchunk(c);
+  fb.tiles1d = (int)tiles_of(c->nd);
+  fb.first = 1;
+  return fb;
+}
+
+// COCG iterations until no system is active.  Expects r (and x) set for the active systems;
+// forms the projector coefficients of r, then iterates the fused kernels.
+template <typename T>
+static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv_all, int maxit) {
   int cnt[kNumStatus];
   int done_iters = 0;
-  for (;;) {
-    for (int j = 0; j < kChunkIters; ++j) CK(cocg_iteration<T>(cv, c->opt.stern_tol, maxit, c->stream));
+  const bool prof = c->opt.profile && c->have_pev && c->prof_stats;
+  FusedBufs<T> fb = make_fused<T>(c);
+  CK(proj_dots<T>(cv_all.nl, cv_all.nd, cv_all.nsys, cv_all.r, cv_all.sysi, 1 << kActive, fb.cr,
+                  c->stream));
+  CK(fused_prepare<T>(cv_all, fb, c->stream));
+  // launches cover only the active systems, listed at every chunk boundary
+  CocgView<T> cv = cv_all;
+  cv.list = c->list_d.as<int>();
+  CKS(counts(c, cv_all.nsys, cnt, true));
+  fb.nact = cnt[kActive];
+  while (fb.nact > 0) {
+    for (int j = 0; j < kChunkIters; ++j) {
+      CK(fused_iteration<T>(cv, fb, c->opt.stern_tol, maxit, c->stream,
+                            prof ? c->pev + 7 * j : nullptr));
+      std::swap(fb.p_in, fb.p_out);
+      fb.first = 0;
+    }
     done_iters += kChunkIters;
-    CKS(counts(c, cv.nsys, cnt));
-    if (cnt[kActive] == 0) break;
+    CKS(counts(c, cv_all.nsys, cnt, true));  // synchronises: the events are complete
+    if (prof) {
+      rpa_stats* st = c->prof_stats;
+      for (int j = 0; j < kChunkIters; ++j) {
+        // interval (i, i+1) of iteration j -> kernel class
+        static const int cls[6] = {0, 1, 2, 3, 2, 4};
+        for (int i = 0; i < 6; ++i) {
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, c->pev[7 * j + i], c->pev[7 * j + i + 1]));
+          st->kernel_seconds[cls[i]] += 1e-3 * ms;
+          st->kernel_launches[cls[i]] += (i == 1 || i == 3) ? 1 : 0;
+        }
+      }
+    }
+    fb.nact = cnt[kActive];
     if (done_iters > maxit + 2 * kChunkIters) break;  // every system is marked by then
   }
   return RPA_OK;
+}
+
+// algorithmic bytes of the COCG kernels from the per-system iteration counts
+static void account_bytes(rpa_ctx* c, long long system_iters, size_t cpxb) {
+  rpa_stats* st = c->prof_stats;
+  if (!st) return;
+  const double pts = (double)system_iters * (double)c->nd;
+  st->kernel_bytes[1] += pts * 4.0 * cpxb;  // direction + H apply: read r, p; write p, w
+  st->kernel_bytes[3] += pts * 6.0 * cpxb;  // update: read x, p, r, w; write x, r
+  st->precision_bytes = (int)(cpxb / 2);
 }
 
 // FP64 form: Galerkin guess, COCG, true-residual recheck with restart (as in the oracle).
@@ -471,6 +554,7 @@ static rpa_status solve_fp64(rpa_ctx* c, int nb, const double* u, const int* act
     if (cnt[kActive] == 0) break;
   }
   CKS(collect_stats(c, S, ss));
+  account_bytes(c, ss.iters, sizeof(cpx<double>));
   CK((density<double, double>(c->nd, c->ns, nb, c->d64.psi.as<double>(), x, active,
                               c->dens64.as<double>(), c->stream)));
   return RPA_OK;
@@ -483,14 +567,18 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
   const int S = nb * c->ns;
   const int maxit = c->opt.stern_maxit;
   const double tol = c->opt.stern_tol;
-  const double itol = c->opt.inner_tol > 0.0 ? c->opt.inner_tol
-                                             : (c->opt.refine > 0 ? std::max(tol, 1e-5) : tol);
+  // FP32 rounds aim at sqrt(tol) (>= 1e-5): short rounds keep the FP32 recurrence in its
+  // accurate regime; FP64 residuals restart them until tol is met.
+  const double itol = c->opt.inner_tol > 0.0
+                          ? c->opt.inner_tol
+                          : (c->opt.refine > 0 ? std::max(std::sqrt(tol), 1e-5) : tol);
   cpx<float>*x = c->x.as<cpx<float>>(), *r = c->r.as<cpx<float>>(), *p = c->p.as<cpx<float>>(),
             *w = c->w.as<cpx<float>>();
   CocgView<float> cv = make_view<float>(c, nb, u32, x, r, p, w);
-  CK(galerkin_guess<float>(c->nd, c->ns, nb, c->d32.psi.as<float>(), c->eps_d.as<double>(),
-                           c->pomega_d.as<double>(), u32, active, c->dV, c->gpart.as<double>(),
-                           gram_chunks(c->nd), c->cmat.as<cpx<float>>(), x, c->stream));
+  CK(galerkin_guess_tc(c->nd, c->ns, nb, c->d32.psi.as<float>(), c->eps_d.as<double>(),
+                       c->pomega_d.as<double>(), u32, active, c->dV, c->gpart.as<double>(),
+                       gram_chunks(c->nd), c->cmat.as<cpx<float>>(), x, c->flags_d.as<int>() + 2,
+                       c->stream));
   CK(set_status(S, c->ns, active, kActive, c->sysi.as<int>(), c->stream));
   CK(proj_dots<float>(cv.nl, c->nd, S, x, cv.sysi, 1 << kActive, cv.cdot, c->stream));
   CK((cocg_resid<float, float>(cv, x, r, p, 1 << kActive, nullptr, nullptr, nullptr, c->stream)));
@@ -499,6 +587,7 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
   CKS(cocg_loop<float>(c, cv, maxit));
   if (c->opt.refine <= 0) {
     CKS(collect_stats(c, S, ss));
+    account_bytes(c, ss.iters, sizeof(cpx<float>));
     CK((density<float, float>(c->nd, c->ns, nb, c->d32.psi.as<float>(), x, active,
                               c->dens64.as<double>(), c->stream)));
     return RPA_OK;
@@ -528,6 +617,7 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
     // systems corrected this round are kConverged again and are re-checked next round.
   }
   CKS(collect_stats(c, S, ss));
+  account_bytes(c, ss.iters, sizeof(cpx<float>));
   CK((density<double, double>(c->nd, c->ns, nb, c->d64.psi.as<double>(), x64, active,
                               c->dens64.as<double>(), c->stream)));
   return RPA_OK;
@@ -670,9 +760,10 @@ static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const d
   std::vector<int> steps(nb);
   CK(cudaMemcpyAsync(steps.data(), c->steps_d.p, sizeof(int) * nb, cudaMemcpyDeviceToHost,
                      c->stream));
-  int flags = 0;
-  CK(cudaMemcpyAsync(&flags, c->flags_d.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  int flags[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(flags, c->flags_d.p, sizeof(flags), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (flags[2]) return fail(c, RPA_ETIMEOUT, "a bounded tensor-core wait expired");
   if (out.steps) std::memcpy(out.steps, steps.data(), sizeof(int) * nb);
   if (st) {
     CKS(timing_add(c, st, 5, 6, 5));
@@ -810,7 +901,7 @@ rpa_status rpa_default_options(rpa_options* o) {
   o->interp = RPA_INTERP_TRICUBIC;
   o->batch = 0;
   o->fkind = RPA_F_LOG;
-  o->refine = 2;
+  o->refine = 4;
   o->inner_tol = 0.0;
   return RPA_OK;
 }
@@ -852,6 +943,9 @@ rpa_status rpa_create(rpa_ctx** out, const rpa_grid* g, void* stream) {
   c->have_events = true;
   for (int i = 0; i < 8; ++i)
     if (cudaEventCreate(&c->ev[i]) != cudaSuccess) c->have_events = false;
+  c->have_pev = true;
+  for (int i = 0; i < 4 * 7; ++i)
+    if (cudaEventCreate(&c->pev[i]) != cudaSuccess) c->have_pev = false;
   make_stencil<double>(c->grid, c->d64.st);
   make_stencil<float>(c->grid, c->d32.st);
   // empty nonlocal part
@@ -875,6 +969,8 @@ void rpa_destroy(rpa_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->have_events)
     for (int i = 0; i < 8; ++i) cudaEventDestroy(c->ev[i]);
+  if (c->have_pev)
+    for (int i = 0; i < 4 * 7; ++i) cudaEventDestroy(c->pev[i]);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -909,8 +1005,16 @@ rpa_status rpa_set_projectors(rpa_ctx* c, int ngroups, const int* nnz, const int
     for (int e = 0; e < z; ++e)
       if (idx[ioff + e] < 0 || idx[ioff + e] >= nd)
         return fail(c, RPA_EINVAL, "projector index out of range");
+    std::vector<int> order(z);
+    for (int e = 0; e < z; ++e) order[e] = e;
+    std::sort(order.begin(), order.end(),
+              [&](int a, int b) { return idx[ioff + a] < idx[ioff + b]; });
+    for (int e = 0; e + 1 < z; ++e)
+      if (idx[ioff + order[e]] == idx[ioff + order[e + 1]])
+        return fail(c, RPA_EINVAL, "duplicate grid index within a projector group");
     for (int l0 = 0; l0 < np; l0 += kProjChunk) {
-      for (int e = 0; e < z; ++e) {
+      for (int oe = 0; oe < z; ++oe) {
+        const int e = order[oe];
         gidx.push_back(idx[ioff + e]);
         for (int l = 0; l < kProjChunk; ++l)
           gchi.push_back(l0 + l < np ? chi[coff + (long long)(l0 + l) * z + e] : 0.0);
@@ -939,6 +1043,34 @@ rpa_status rpa_set_projectors(rpa_ctx* c, int ngroups, const int* nnz, const int
       pgrp[slot] = g;
       for (int l = 0; l < kProjChunk; ++l) pchi[(size_t)slot * kProjChunk + l] = gchi[(size_t)e * kProjChunk + l];
     }
+  // per 1-D COCG tile (kTile consecutive points): for every group with entries in the tile,
+  // the contiguous range of its (index-sorted) group-major entries that falls in the tile
+  const long long ntile = (nd + kTile - 1) / kTile;
+  std::vector<int> troff(ntile + 1, 0), trng;
+  {
+    std::vector<std::vector<int>> per(ntile);
+    for (int g = 0; g < NG; ++g) {
+      int e = goff[g];
+      while (e < goff[g + 1]) {
+        const long long t = gidx[e] / kTile;
+        int f = e;
+        while (f < goff[g + 1] && gidx[f] / kTile == t) ++f;
+        per[t].push_back(g);
+        per[t].push_back(e);
+        per[t].push_back(f);
+        e = f;
+      }
+    }
+    for (long long t = 0; t < ntile; ++t) {
+      troff[t + 1] = troff[t] + (int)(per[t].size() / 3);
+      trng.insert(trng.end(), per[t].begin(), per[t].end());
+    }
+  }
+  if (trng.empty()) trng.assign(3, 0);
+  CK(c->tile_roff.ensure(sizeof(int) * troff.size()));
+  CK(c->tile_ranges.ensure(sizeof(int) * trng.size()));
+  CK(cudaMemcpy(c->tile_roff.p, troff.data(), sizeof(int) * troff.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->tile_ranges.p, trng.data(), sizeof(int) * trng.size(), cudaMemcpyHostToDevice));
   std::vector<float> gchi_f(gchi.begin(), gchi.end()), gcoef_f(gcoef.begin(), gcoef.end()),
       pchi_f(pchi.begin(), pchi.end());
   const size_t Eb = std::max<long long>(E, 1);
@@ -972,9 +1104,10 @@ rpa_status rpa_set_occupied(rpa_ctx* c, int ns, const double* psi, const double*
   if (!c || !psi || !eps || ns < 1 || ns > 1024) return RPA_EINVAL;
   CK(cudaSetDevice(c->device));
   std::vector<double> e(ns);
-  if (where == RPA_DEVICE)
-    CK(cudaMemcpy(e.data(), eps, sizeof(double) * ns, cudaMemcpyDeviceToHost));
-  else
+  if (where == RPA_DEVICE) {
+    CK(cudaMemcpyAsync(e.data(), eps, sizeof(double) * ns, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  } else
     std::memcpy(e.data(), eps, sizeof(double) * ns);
   for (int i = 0; i + 1 < ns; ++i)
     if (!(e[i] <= e[i + 1])) return fail(c, RPA_ENOGAP, "eps must be ascending");
@@ -1067,8 +1200,11 @@ rpa_status rpa_probe_density(rpa_ctx* c, int count, const long long* probe, cons
   std::vector<int> fq(count);
   if (where == RPA_DEVICE) {
     if (count > 0) {
-      CK(cudaMemcpy(pr.data(), probe, sizeof(long long) * count, cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(fq.data(), freq, sizeof(int) * count, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpyAsync(pr.data(), probe, sizeof(long long) * count, cudaMemcpyDeviceToHost,
+                         c->stream));
+      CK(cudaMemcpyAsync(fq.data(), freq, sizeof(int) * count, cudaMemcpyDeviceToHost,
+                         c->stream));
+      CK(cudaStreamSynchronize(c->stream));
     }
   } else {
     std::memcpy(pr.data(), probe, sizeof(long long) * count);
@@ -1081,12 +1217,16 @@ rpa_status rpa_probe_density(rpa_ctx* c, int count, const long long* probe, cons
     om[i] = c->omega[fq[i]];
   }
   if (st) std::memset(st, 0, sizeof(*st));
+  c->prof_stats = st;
   const int nl = c->opt.lanczos_max;
   std::vector<double> dh(count), ah(alpha ? (size_t)count * nl : 0), bh(beta ? (size_t)count * nl : 0);
   std::vector<int> sh(steps ? count : 0);
   bool nonconv = false;
-  CKS(run_probes(c, count, pr.data(), om.data(), dh.data(), alpha ? ah.data() : nullptr,
-                 beta ? bh.data() : nullptr, steps ? sh.data() : nullptr, st, &nonconv));
+  rpa_status rs = run_probes(c, count, pr.data(), om.data(), dh.data(),
+                             alpha ? ah.data() : nullptr, beta ? bh.data() : nullptr,
+                             steps ? sh.data() : nullptr, st, &nonconv);
+  c->prof_stats = nullptr;
+  CKS(rs);
   CKS(copy_out(c, d, dh.data(), sizeof(double) * count, where));
   if (alpha) CKS(copy_out(c, alpha, ah.data(), sizeof(double) * count * nl, where));
   if (beta) CKS(copy_out(c, beta, bh.data(), sizeof(double) * count * nl, where));
@@ -1120,6 +1260,7 @@ rpa_status rpa_energy_density(rpa_ctx* c, double* d_coarse, double* d_fine, doub
   CKS(check_ready(c, true));
   auto t0 = std::chrono::steady_clock::now();
   if (st) std::memset(st, 0, sizeof(*st));
+  c->prof_stats = st;
   const long long P = num_probes(c);
   std::vector<long long> idx(P);
   CKS(rpa_probe_indices(c, idx.data()));
@@ -1132,8 +1273,10 @@ rpa_status rpa_energy_density(rpa_ctx* c, double* d_coarse, double* d_fine, doub
       om[k * P + j] = c->omega[k];
     }
   bool nonconv = false;
-  CKS(run_probes(c, count, pr.data(), om.data(), dh.data(), nullptr, nullptr, nullptr, st,
-                 &nonconv));
+  rpa_status rs = run_probes(c, count, pr.data(), om.data(), dh.data(), nullptr, nullptr,
+                             nullptr, st, &nonconv);
+  c->prof_stats = nullptr;
+  CKS(rs);
   auto t1 = std::chrono::steady_clock::now();
   DevBuf dco, dfi, ecd;
   CK(dco.ensure(sizeof(double) * count));
@@ -1222,9 +1365,11 @@ rpa_status rpa_chi0(rpa_ctx* c, int count, const double* omega, const double* u,
   const int nb_max = choose_batch(c, count);
   CKS(ensure_workspace(c, nb_max));
   std::vector<double> om(count);
-  if (where == RPA_DEVICE)
-    CK(cudaMemcpy(om.data(), omega, sizeof(double) * count, cudaMemcpyDeviceToHost));
-  else
+  if (where == RPA_DEVICE) {
+    CK(cudaMemcpyAsync(om.data(), omega, sizeof(double) * count, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  } else
     std::memcpy(om.data(), omega, sizeof(double) * count);
   for (int i = 0; i < count; ++i)
     if (!(om[i] > 0.0)) return fail(c, RPA_EINVAL, "omega must be positive");
@@ -1257,6 +1402,57 @@ rpa_status rpa_chi0(rpa_ctx* c, int count, const double* omega, const double* u,
     CK(cudaStreamSynchronize(c->stream));
   }
   if (nonconv) return fail(c, RPA_ENOCONV, "a Sternheimer solve reached stern_maxit");
+  return RPA_OK;
+}
+
+rpa_status rpa_galerkin(rpa_ctx* c, int count, const double* omega, const double* u, double* x0,
+                        int where) {
+  CKS(check_ready(c, false));
+  if (count < 0 || (count > 0 && (!omega || !u || !x0))) return fail(c, RPA_EINVAL, "bad arguments");
+  if (count == 0) return RPA_OK;
+  const int nb_max = choose_batch(c, count);
+  CKS(ensure_workspace(c, nb_max));
+  std::vector<double> om(count);
+  if (where == RPA_DEVICE) {
+    CK(cudaMemcpyAsync(om.data(), omega, sizeof(double) * count, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  } else {
+    std::memcpy(om.data(), omega, sizeof(double) * count);
+  }
+  const long long nd = c->nd;
+  DevBuf xo;
+  CK(xo.ensure(sizeof(cpx<double>) * (size_t)nb_max * c->ns * nd));
+  CK(cudaMemsetAsync(c->flags_d.p, 0, sizeof(int) * 4, c->stream));
+  for (int s0 = 0; s0 < count; s0 += nb_max) {
+    const int nb = std::min(nb_max, count - s0);
+    std::vector<int> ones(nb, 1);
+    CK(cudaMemcpyAsync(c->active_d.p, ones.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->pomega_d.p, om.data() + s0, sizeof(double) * nb, cudaMemcpyHostToDevice,
+                       c->stream));
+    CKS(copy_in(c, c->u64.p, u + (long long)s0 * nd, sizeof(double) * nb * nd, where));
+    const long long n = (long long)nb * c->ns * nd;
+    if (c->opt.precision == RPA_MIXED) {
+      CK(convert_d2f(c->u64.as<double>(), c->u32.as<float>(), (long long)nb * nd, c->stream));
+      CK(galerkin_guess_tc(nd, c->ns, nb, c->d32.psi.as<float>(), c->eps_d.as<double>(),
+                           c->pomega_d.as<double>(), c->u32.as<float>(), c->active_d.as<int>(),
+                           c->dV, c->gpart.as<double>(), gram_chunks(nd),
+                           c->cmat.as<cpx<float>>(), c->x.as<cpx<float>>(),
+                           c->flags_d.as<int>() + 2, c->stream));
+      CK(convert_f2d(c->x.as<float>(), xo.as<double>(), 2 * n, c->stream));
+    } else {
+      CK(galerkin_guess<double>(nd, c->ns, nb, c->d64.psi.as<double>(), c->eps_d.as<double>(),
+                                c->pomega_d.as<double>(), c->u64.as<double>(),
+                                c->active_d.as<int>(), c->dV, c->gpart.as<double>(),
+                                gram_chunks(nd), c->cmat.as<cpx<double>>(),
+                                xo.as<cpx<double>>(), c->stream));
+    }
+    CKS(copy_out(c, x0 + 2 * (long long)s0 * c->ns * nd, xo.p, sizeof(cpx<double>) * n, where));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  int flags[4];
+  CK(cudaMemcpy(flags, c->flags_d.p, sizeof(flags), cudaMemcpyDeviceToHost));
+  if (flags[2]) return fail(c, RPA_ETIMEOUT, "a bounded tensor-core wait expired");
   return RPA_OK;
 }
 

@@ -218,84 +218,6 @@ __global__ void __launch_bounds__(256) k_resid(CocgView<T> cv, const cpx<T>* __r
   }
 }
 
-// w = A p, partial mu = p^T w
-template <typename T>
-__global__ void __launch_bounds__(256) k_matvec(CocgView<T> cv) {
-  const int s = blockIdx.y;
-  if (status_of(cv.sysi, s) != kActive) return;
-  __shared__ double sh[8 * 2];
-  const int b = s / cv.ns, n = s - b * cv.ns;
-  const long long nd = cv.nd;
-  const cpx<T> sigma = mk<T>((T)cv.eps[n], (T)cv.omega[b]);
-  const cpx<T>* ps = cv.p + (long long)s * nd;
-  const cpx<T>* cd = cv.cdot + (long long)s * cv.nl.ngroup * kProjChunk;
-  double acc[2] = {0.0, 0.0};
-  const long long t0 = (long long)blockIdx.x * kTile;
-  const long long t1 = min(t0 + kTile, nd);
-  for (long long p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
-    int ix, iy, iz;
-    point_coords(p, cv.st, ix, iy, iz);
-    const cpx<T> wv = h_at(cv.st, cv.vloc, cv.nl, ps, cd, ix, iy, iz, p, sigma);
-    cv.w[(long long)s * nd + p] = wv;
-    const cpx<T> pv = ps[p];
-    acc[0] += (double)pv.re * wv.re - (double)pv.im * wv.im;
-    acc[1] += (double)pv.re * wv.im + (double)pv.im * wv.re;
-  }
-  block_reduce<2>(acc, sh);
-  if (threadIdx.x == 0) {
-    double* pp = cv.part + ((long long)s * cv.tiles + blockIdx.x) * 4;
-    pp[0] = acc[0];
-    pp[1] = acc[1];
-  }
-}
-
-// x += alpha p, r -= alpha w, partials ||r||^2, r^T r
-template <typename T>
-__global__ void __launch_bounds__(256) k_update(CocgView<T> cv) {
-  const int s = blockIdx.y;
-  if (status_of(cv.sysi, s) != kActive) return;
-  __shared__ double sh[8 * 3];
-  const long long nd = cv.nd;
-  const double* sd = cv.sysd + (long long)s * kSysD;
-  const cpx<T> al = mk<T>((T)sd[kAlpha], (T)sd[kAlpha + 1]);
-  double acc[3] = {0.0, 0.0, 0.0};
-  const long long t0 = (long long)blockIdx.x * kTile;
-  const long long t1 = min(t0 + kTile, nd);
-  for (long long p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
-    const long long q = (long long)s * nd + p;
-    const cpx<T> pv = cv.p[q], wv = cv.w[q];
-    cv.x[q] = cadd(cv.x[q], cmul(al, pv));
-    const cpx<T> rv = csub(cv.r[q], cmul(al, wv));
-    cv.r[q] = rv;
-    acc[0] += (double)rv.re * rv.re + (double)rv.im * rv.im;
-    acc[1] += (double)rv.re * rv.re - (double)rv.im * rv.im;
-    acc[2] += 2.0 * (double)rv.re * rv.im;
-  }
-  block_reduce<3>(acc, sh);
-  if (threadIdx.x == 0) {
-    double* pp = cv.part + ((long long)s * cv.tiles + blockIdx.x) * 4;
-    pp[0] = acc[0];
-    pp[2] = acc[1];
-    pp[3] = acc[2];
-  }
-}
-
-// p = r + beta p
-template <typename T>
-__global__ void __launch_bounds__(256) k_direction(CocgView<T> cv) {
-  const int s = blockIdx.y;
-  if (status_of(cv.sysi, s) != kActive) return;
-  const long long nd = cv.nd;
-  const double* sd = cv.sysd + (long long)s * kSysD;
-  const cpx<T> be = mk<T>((T)sd[kBeta], (T)sd[kBeta + 1]);
-  const long long t0 = (long long)blockIdx.x * kTile;
-  const long long t1 = min(t0 + kTile, nd);
-  for (long long p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
-    const long long q = (long long)s * nd + p;
-    cv.p[q] = cadd(cv.r[q], cmul(be, cv.p[q]));
-  }
-}
-
 // -------------------------------------------------------------------------------------------
 // per-system scalar steps (one warp per system, partial sums added in tile order)
 // -------------------------------------------------------------------------------------------
@@ -318,18 +240,20 @@ __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi,
 // kind: 0 init after the first residual (target = tol ||b||, or round target for
 //        refinement), 1 alpha, 2 beta/convergence, 3 true-residual recheck,
 //        4 refinement check (FP64 residual of the mixed form)
-__global__ void k_scalars(int nsys, int tiles, const double* __restrict__ part, double* sysd,
-                          int* sysi, int kind, int mask, double tol, double inner_tol,
-                          int maxit, int max_restart) {
-  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+__global__ void k_scalars(int nsys, int tiles, int stride, const double* __restrict__ part,
+                          double* sysd, int* sysi, int kind, int mask, double tol,
+                          double inner_tol, int maxit, int max_restart,
+                          const int* __restrict__ list) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (s >= nsys) return;
+  if (i >= nsys) return;
+  const int s = list ? list[i] : i;
   int* si = sysi + (long long)s * kSysI;
   double* sd = sysd + (long long)s * kSysD;
   const int st = si[kStatus];
   if (!((mask >> st) & 1)) return;
   double v[4];
-  warp_sum_tiles(part + (long long)s * tiles * 4, tiles, lane, v);
+  warp_sum_tiles(part + (long long)s * stride * 4, tiles, lane, v);
   if (lane != 0) return;
   if (kind == 0) {  // after r0 = b - A x0
     const double rn = sqrt(v[0]), bn = sqrt(v[1]);
@@ -412,11 +336,16 @@ __global__ void k_scalars(int nsys, int tiles, const double* __restrict__ part, 
 }
 
 // counts of systems per status
-__global__ void k_count_status(int nsys, const int* __restrict__ sysi, int* __restrict__ counts) {
+__global__ void k_count_status(int nsys, const int* __restrict__ sysi, int* __restrict__ counts,
+                               int* __restrict__ list) {
   __shared__ int sc[kNumStatus];
   if (threadIdx.x < kNumStatus) sc[threadIdx.x] = 0;
   __syncthreads();
-  for (int s = threadIdx.x; s < nsys; s += blockDim.x) atomicAdd(&sc[sysi[(long long)s * kSysI + kStatus]], 1);
+  for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
+    const int st = sysi[(long long)s * kSysI + kStatus];
+    const int pos = atomicAdd(&sc[st], 1);
+    if (list && st == kActive) list[pos] = s;
+  }
   __syncthreads();
   if (threadIdx.x < kNumStatus) counts[threadIdx.x] = sc[threadIdx.x];
 }
@@ -509,34 +438,19 @@ cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t cocg_iteration(const CocgView<T>& cv, double tol, int maxit, cudaStream_t s) {
-  dim3 grid(cv.tiles, cv.nsys);
-  cudaError_t e = proj_dots<T>(cv.nl, cv.nd, cv.nsys, cv.p, cv.sysi, 1 << kActive, cv.cdot, s);
-  if (e != cudaSuccess) return e;
-  k_matvec<T><<<grid, 256, 0, s>>>(cv);
-  const int sblocks = (cv.nsys + 3) / 4;
-  k_scalars<<<sblocks, 128, 0, s>>>(cv.nsys, cv.tiles, cv.part, cv.sysd, cv.sysi, 1,
-                                    1 << kActive, tol, 0.0, maxit, 0);
-  k_update<T><<<grid, 256, 0, s>>>(cv);
-  k_scalars<<<sblocks, 128, 0, s>>>(cv.nsys, cv.tiles, cv.part, cv.sysd, cv.sysi, 2,
-                                    1 << kActive, tol, 0.0, maxit, 0);
-  k_direction<T><<<grid, 256, 0, s>>>(cv);
-  note_launch(5);
-  return cudaGetLastError();
-}
-
 cudaError_t cocg_scalars(int nsys, int tiles, const double* part, double* sysd, int* sysi,
                          int kind, int mask, double tol, double inner_tol, int maxit,
-                         int max_restart, cudaStream_t s) {
-  k_scalars<<<(nsys + 3) / 4, 128, 0, s>>>(nsys, tiles, part, sysd, sysi, kind, mask, tol,
-                                           inner_tol, maxit, max_restart);
+                         int max_restart, cudaStream_t s, int stride, const int* list) {
+  if (nsys <= 0) return cudaSuccess;
+  k_scalars<<<(nsys + 3) / 4, 128, 0, s>>>(nsys, tiles, stride > 0 ? stride : tiles, part, sysd,
+                                           sysi, kind, mask, tol, inner_tol, maxit, max_restart,
+                                           list);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t count_status(int nsys, const int* sysi, int* counts, cudaStream_t s) {
-  k_count_status<<<1, 1024, 0, s>>>(nsys, sysi, counts);
+cudaError_t count_status(int nsys, const int* sysi, int* counts, cudaStream_t s, int* list) {
+  k_count_status<<<1, 1024, 0, s>>>(nsys, sysi, counts, list);
   note_launch();
   return cudaGetLastError();
 }
@@ -595,8 +509,6 @@ template cudaError_t cocg_resid<double, float>(const CocgView<double>&, const cp
 template cudaError_t cocg_resid<float, float>(const CocgView<float>&, const cpx<float>*,
                                               cpx<float>*, cpx<float>*, int, cpx<float>*,
                                               cpx<float>*, cpx<float>*, cudaStream_t);
-template cudaError_t cocg_iteration<double>(const CocgView<double>&, double, int, cudaStream_t);
-template cudaError_t cocg_iteration<float>(const CocgView<float>&, double, int, cudaStream_t);
 template cudaError_t accumulate<double, float>(long long, int, const int*, int, int,
                                                const cpx<float>*, cpx<double>*, int, cudaStream_t);
 template cudaError_t density<double, double>(long long, int, int, const double*,

@@ -35,6 +35,7 @@ struct CocgView {
   double* part;          // nsys x tiles x 4
   double* sysd;          // nsys x kSysD
   int* sysi;             // nsys x kSysI
+  const int* list;       // optional: compacted indices of the active systems (grid.y)
 };
 
 template <typename T>
@@ -47,12 +48,18 @@ cudaError_t apply_h(const Stencil<T>& st, const T* vloc, const NonlocalDev<T>& n
 template <typename T, typename TL>
 cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
                        cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s);
-template <typename T>
-cudaError_t cocg_iteration(const CocgView<T>& cv, double tol, int maxit, cudaStream_t s);
+// Per-system scalar step (kind: 0 init, 1 alpha, 2 beta/convergence, 3 true-residual
+// recheck, 4 FP64 refinement check, 5 mixed-form init).  `tiles` partial sums per system are
+// added; `stride` (default tiles) is the per-system stride of the partial-sum buffer.
+// With list != null, nsys is the length of the list and the step runs for listed systems.
 cudaError_t cocg_scalars(int nsys, int tiles, const double* part, double* sysd, int* sysi,
                          int kind, int mask, double tol, double inner_tol, int maxit,
-                         int max_restart, cudaStream_t s);
-cudaError_t count_status(int nsys, const int* sysi, int* counts, cudaStream_t s);
+                         int max_restart, cudaStream_t s, int stride = 0,
+                         const int* list = nullptr);
+// counts[status] over all systems; with list != null also writes the indices of the
+// active systems (order unspecified) to list[0 .. counts[kActive])
+cudaError_t count_status(int nsys, const int* sysi, int* counts, cudaStream_t s,
+                         int* list = nullptr);
 cudaError_t set_status(int nsys, int ns, const int* probe_active, int on, int* sysi,
                        cudaStream_t s);
 cudaError_t remap_status(int nsys, int from, int to, int* sysi, cudaStream_t s);
@@ -72,6 +79,12 @@ template <typename T>
 cudaError_t galerkin_guess(long long nd, int ns, int nb, const T* psi, const double* eps,
                            const double* omega, const T* u, const int* probe_active, double dV,
                            double* gpart, int nchunk, cpx<T>* cmat, cpx<T>* x0, cudaStream_t s);
+// The same projection on the tensor cores (umma.cu, tcgen05 kind::tf32, 3-pass tf32 split):
+// FP32 operands, FP32 results; err receives 1 if a bounded tensor-core wait expired.
+cudaError_t galerkin_guess_tc(long long nd, int ns, int nb, const float* psi, const double* eps,
+                              const double* omega, const float* u, const int* probe_active,
+                              double dV, double* gpart, int nchunk, cpx<float>* cmat,
+                              cpx<float>* x0, int* err, cudaStream_t s);
 // Mode products along one axis of a batch of 3-D arrays: out[..a..] = sum_i Mt[i][a] in[..i..]
 // (Mt is nin x nout, row-major).  dims_in = (nx, ny, nz) of the input; batch strides in_bs and
 // out_bs.  Optional elementwise scale of the output (same layout as the output).

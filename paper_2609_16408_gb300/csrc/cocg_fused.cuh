@@ -1,0 +1,27 @@
+// Fused COCG iteration: declarations.
+#pragma once
+#include "cocg.cuh"
+
+namespace rpa {
+
+
+template <typename T>
+struct FusedBufs {
+  cpx<T>* p_in;            // p_{k-1}
+  cpx<T>* p_out;           // p_k
+  cpx<T>* cp;              // projector coefficients of p_k (gamma dV chi^T p), nsys x ng x 4
+  cpx<T>* cr;              // projector sums of r, accumulated by the update kernel
+  const int* tile_roff;    // per 1-D tile: offsets into the range list
+  const int* tile_ranges;  // (group, first entry, end entry) of group-major entries in a tile
+  int ntiles_xy, nzchunk, zchunk, tiles1d, first;
+  int nact;                // launched systems: the first nact entries of CocgView::list
+};
+
+template <typename T>
+cudaError_t fused_iteration(const CocgView<T>& cv, const FusedBufs<T>& fb, double tol, int maxit,
+                            cudaStream_t s, cudaEvent_t* ev = nullptr);
+// cp = cr, cr = 0 for every active system (start of a solve or restart)
+template <typename T>
+cudaError_t fused_prepare(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s);
+
+}  // namespace rpa

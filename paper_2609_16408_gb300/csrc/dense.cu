@@ -159,6 +159,17 @@ cudaError_t galerkin_guess(long long nd, int ns, int nb, const T* psi, const dou
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t gram_coef(int ns, int nb, int nchunk, const double* gpart, const double* eps,
+                      const double* omega, const int* active, double dV, cpx<T>* cmat,
+                      cudaStream_t s) {
+  dim3 g2((ns * ns + 255) / 256, nb);
+  k_gram_coef<T><<<g2, 256, 0, s>>>(ns, nchunk, gpart, eps, omega, active, dV, cmat);
+  return cudaGetLastError();
+}
+template cudaError_t gram_coef<float>(int, int, int, const double*, const double*, const double*,
+                                      const int*, double, cpx<float>*, cudaStream_t);
+
 // -------------------------------------------------------------------------------------------
 // mode products: out[.., a, ..] = sum_i Mt[i][a] in[.., i, ..] along one axis
 // -------------------------------------------------------------------------------------------

@@ -21,7 +21,9 @@ Recipe (stated here so the inputs can be rebuilt from seeds alone):
 * Ground state: the lowest ``ns`` eigenpairs of ``H = -1/2 Lap_h + V_loc + V_nl`` where
   ``Lap_h`` is the central finite-difference Laplacian of radius ``fd_radius``.  Orbitals are
   normalised as ``dV * sum psi^2 = 1``.  A system is re-seeded until the gap
-  ``eps_{ns+1} - eps_ns`` reaches ``min_gap`` so that the occupied set is well defined.
+  ``eps_{ns+1} - eps_ns`` reaches ``min_gap`` so that the occupied set is well defined
+  (0.05 Ha for the toy cell; 0.01 Ha for the Si-like cells, whose 64-atom model has a
+  Gamma-point gap of about 0.013 Ha, the size of a real Si64 cell's gap at Gamma).
 
 The finite-difference weights used for the eigenproblem come from an exact rational solve
 of the moment (Vandermonde) conditions, independent of how the oracle or the CUDA library
@@ -38,7 +40,7 @@ from fractions import Fraction
 import numpy as np
 
 PERIODIC, DIRICHLET = 0, 1
-_CACHE_VERSION = 3
+_CACHE_VERSION = 4
 
 
 # ----------------------------------------------------------------------------------------
@@ -219,7 +221,8 @@ def diamond_sites(a: float, ncell=(1, 1, 1)) -> np.ndarray:
 # ground state
 # ----------------------------------------------------------------------------------------
 class _PeriodicH:
-    """H applied to blocks (m, N_d) with the kinetic term diagonal in the discrete Fourier basis."""
+    """H applied to blocks X of shape (N_d, m) (points x vectors); the kinetic term is
+    diagonal in the discrete Fourier basis."""
 
     def __init__(self, s: System):
         nx, ny, nz = s.n
@@ -235,16 +238,25 @@ class _PeriodicH:
 
     def __call__(self, X):
         import scipy.fft as sfft
-        m = X.shape[0]
-        F = sfft.rfftn(X.reshape((m,) + self.shape), axes=(1, 2, 3), workers=-1)
-        F *= self.K[None]
-        Y = sfft.irfftn(F, s=self.shape, axes=(1, 2, 3), workers=-1).reshape(m, -1)
-        Y += X * self.v[None, :]
+        m = X.shape[1]
+        F = sfft.rfftn(X.reshape(self.shape + (m,)), axes=(0, 1, 2), workers=-1)
+        F *= self.K[..., None]
+        Y = sfft.irfftn(F, s=self.shape, axes=(0, 1, 2), workers=-1).reshape(-1, m)
+        Y += X * self.v[:, None]
         for g in self.groups:
-            xb = X[:, g.idx]                             # (m, nnz)
-            c = (xb @ g.chi.T) * (self.dV * g.gamma)     # (m, nproj)
-            Y[:, g.idx] += c @ g.chi
+            xb = X[g.idx, :]                                   # (nnz, m)
+            c = (g.chi @ xb) * (self.dV * g.gamma)[:, None]    # (nproj, m)
+            Y[g.idx, :] += g.chi.T @ c
         return Y
+
+
+def _orth(Y):
+    """Orthonormal basis of the columns of Y (N x m) by two Cholesky-QR passes."""
+    for _ in range(2):
+        S = Y.T @ Y
+        L = np.linalg.cholesky(0.5 * (S + S.T))
+        Y = np.linalg.solve(L, Y.T).T
+    return Y
 
 
 def _lanczos_max(Hop, N, rng, steps=40):
@@ -255,7 +267,7 @@ def _lanczos_max(Hop, N, rng, steps=40):
     b = 0.0
     qprev = np.zeros(N)
     for _ in range(steps):
-        w = Hop(q[None, :])[0]
+        w = Hop(q[:, None])[:, 0]
         a = q @ w
         w = w - a * q - b * qprev
         for v in Q:
@@ -271,18 +283,17 @@ def _lanczos_max(Hop, N, rng, steps=40):
 
 
 def _chfsi(s: System, m: int, tol: float, seed: int, degree=24, maxit=200, log=None):
-    """Chebyshev-filtered subspace iteration for the lowest m eigenpairs (l2 normalised)."""
+    """Chebyshev-filtered subspace iteration for the lowest m eigenpairs (l2 normalised).
+    Returns (ritz values, vectors as rows (m, N_d), max residual of the first ns)."""
     Hop = _PeriodicH(s)
     N = s.N_d
     rng = np.random.default_rng(seed)
     bmax = _lanczos_max(Hop, N, rng)
-    X = rng.standard_normal((m, N))
-    X, _ = np.linalg.qr(X.T)
-    X = X.T
+    X = _orth(rng.standard_normal((N, m)))
     HX = Hop(X)
-    th, W = np.linalg.eigh(X @ HX.T)
-    X = W.T @ X
-    HX = W.T @ HX
+    th, W = np.linalg.eigh(X.T @ HX)
+    X = X @ W
+    HX = HX @ W
     a = float(th[-1])
     a0 = float(th[0])
     res = np.inf
@@ -299,15 +310,14 @@ def _chfsi(s: System, m: int, tol: float, seed: int, degree=24, maxit=200, log=N
             Yn = (2.0 * (Hop(Y) - c * Y) / e * rho - rho_prev * Yp) / rho_next
             Yp, Y = Y, Yn
             rho_prev, rho = rho, rho_next
-        Q, _ = np.linalg.qr(Y.T)
-        Q = Q.T
+        Q = _orth(Y)
         HQ = Hop(Q)
-        S = Q @ HQ.T
+        S = Q.T @ HQ
         th, W = np.linalg.eigh(0.5 * (S + S.T))
-        X = W.T @ Q
-        HX = W.T @ HQ
-        R = HX - th[:, None] * X
-        rn = np.linalg.norm(R, axis=1)
+        X = Q @ W
+        HX = HQ @ W
+        R = HX - X * th[None, :]
+        rn = np.linalg.norm(R, axis=0)
         res = float(rn[: s.ns].max())
         if log:
             log(f"chfsi it {it} res {res:.3e} ritz[ns-1..ns] {th[s.ns - 1]:.6f} {th[s.ns]:.6f}")
@@ -315,7 +325,7 @@ def _chfsi(s: System, m: int, tol: float, seed: int, degree=24, maxit=200, log=N
             break
         a = float(th[-1])
         a0 = float(th[0])
-    return th, X, res
+    return th, X.T, res
 
 
 def _solve_ground_state(s: System, tol=1e-10, seed=0, log=None):
@@ -464,7 +474,7 @@ def toy_system(seed=0, n=12, L=6.0, ns=8, fd_radius=6, nwell=4, **kw):
 def si_like_system(ncell=(1, 1, 1), a=10.26, pts_per_cell=26, ns=None, seed=1,
                    depth=(1.2, 1.8), sigma=1.0, proj_sigma=1.1,
                    gamma_rng=((1.5, 2.5), (-3.5, -2.5)),
-                   fd_radius=6, **kw):
+                   fd_radius=6, min_gap=0.01, **kw):
     """Perturbed diamond-Si-like cell: Gaussian wells plus 4 s/p projectors per atom."""
     n = tuple(pts_per_cell * c for c in ncell)
     L = tuple(a * c for c in ncell)
@@ -483,7 +493,7 @@ def si_like_system(ncell=(1, 1, 1), a=10.26, pts_per_cell=26, ns=None, seed=1,
     name = f"si{nat}_{'x'.join(map(str, n))}"
     return gaussian_system(name, n, L, (PERIODIC,) * 3, None, None, None, ns,
                            fd_radius=fd_radius, proj_sigma=proj_sigma, gamma_rng=gamma_rng,
-                           seed=seed, _positions_fn=pos, **kw)
+                           seed=seed, min_gap=min_gap, _positions_fn=pos, **kw)
 
 
 def cluster_system(natom=12, box=16.0, n=40, ns=24, seed=6, fd_radius=6, **kw):

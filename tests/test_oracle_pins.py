@@ -325,3 +325,26 @@ def test_fourier_interpolation_exact_on_bandlimited():
 def test_error_metrics_definition():
     m = oracle.error_metrics(np.array([1.0, 2.0, 3.0]), np.array([1.5, 1.5, 3.0]))
     assert m["abs_err"] == 0.0 and m["l1"] == 1.0 and m["ecr"] == 0.0
+
+
+@pytest.mark.parametrize("bc", [(PERIODIC,) * 3, (DIRICHLET,) * 3])
+def test_galerkin_guess_satisfies_galerkin_condition(bc):
+    """x0 lies in span(Psi) and its residual is orthogonal to span(Psi) (dV inner product),
+    checked with the generator's dense H; and x0 adds nothing to the density (the occupied
+    pairs cancel by antisymmetry)."""
+    s = tiny(bc=bc, ns=3)
+    H = s.dense_h()
+    rng = np.random.default_rng(10)
+    u = rng.standard_normal(s.N_d)
+    om = 0.31
+    x0 = oracle.galerkin(s, om, u)
+    for n in range(s.ns):
+        b = -s.psi[n] * u
+        res = H @ x0[n] - (s.eps[n] + 1j * om) * x0[n] - b
+        proj = s.dV * (s.psi @ res)
+        assert np.max(np.abs(proj)) < 1e-10 * np.max(np.abs(s.dV * (s.psi @ b)))
+        # x0 is a combination of the occupied orbitals
+        coef = s.dV * (s.psi @ x0[n])
+        assert np.allclose(s.psi.T @ coef, x0[n], atol=1e-12 * np.abs(x0[n]).max())
+    dens = 4 * np.sum(s.psi * np.real(x0), axis=0)
+    assert np.max(np.abs(dens)) < 1e-12 * np.max(np.abs(x0))
