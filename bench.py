@@ -275,14 +275,20 @@ def run_ours(args, wl):
     dom = 1 if ks[1] >= ks[3] else 3
     pk = peaks()
     achieved = kb[dom] / ks[dom] / 1e9 if ks[dom] > 0 else 0.0
+    # DRAM traffic per launch from the committed ncu capture (dram__bytes_read + write of one
+    # launch, divided by the systems active in that launch), scaled to this run's average
+    # number of active systems per launch; null once the kernel sources have changed.
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
+    if os.path.exists(tr_path) and kl[dom] > 0:
         tj = json.load(open(tr_path)).get(names[dom])
         if tj and tj.get("source_sha") == kernel_source_sha():
-            traffic = tj.get("bytes_per_launch")
+            alg_per_sys = {1: 4, 3: 6}[dom] * 2 * stats[0]["precision_bytes"] * nd
+            sys_per_launch = kb[dom] / alg_per_sys / kl[dom]
+            traffic = tj["dram_bytes_per_system"] * sys_per_launch
     roofline = dict(bound="hbm", kernel=names[dom], achieved=achieved, peak=pk["hbm_gbs"],
                     unit="GB/s", frac=achieved / pk["hbm_gbs"], traffic=traffic,
+                    algorithmic_bytes_per_launch=float(kb[dom] / max(1, kl[dom])),
                     peak_src=pk["src"] + " (burst copy)",
                     launches=int(kl[dom]), seconds=float(ks[dom]),
                     algorithmic_bytes=float(kb[dom]),

@@ -161,6 +161,13 @@ rpa_status rpa_probe_indices(rpa_ctx *ctx, long long *idx);
 rpa_status rpa_energy_density(rpa_ctx *ctx, double *d_coarse, double *d_fine, double *ec,
                               rpa_stats *stats, int where);
 
+/* E_c of several independent systems (contexts of possibly different grids, boundary
+ * conditions, occupied sets and options) in one call: each context runs rpa_energy_density
+ * on its own stream from its own host thread, so their kernels overlap on the GPU.
+ * ec_out (nsys doubles, host) receives each system's E_c; stats (nsys entries or NULL).
+ * The contexts must be distinct.  Returns the first non-OK status of any system. */
+rpa_status rpa_batch_energy(int nsys, rpa_ctx *const *sys, double *ec_out, rpa_stats *stats);
+
 /* Lanczos quadrature for an explicit list of probe-points: probe[i] is a fine-grid index,
  * freq[i] an index into the frequency list.  d (count doubles) receives d_j(i w).  When
  * alpha/beta are non-NULL they receive the tridiagonal entries (count x lanczos_max, zero

@@ -141,6 +141,7 @@ def _declare(lib):
         "rpa_chi0": ([P, I, P, P, P, P, I], I),
         "rpa_tridiag_f11": ([I, I, P, P, I, P], I),
         "rpa_galerkin": ([P, I, P, P, P, I], I),
+        "rpa_batch_energy": ([I, P, P, P], I),
         "rpa_status_string": ([I], C.c_char_p),
         "rpa_last_error": ([P], C.c_char_p),
         "rpa_kernel_launches": ([P], LL),
@@ -338,6 +339,17 @@ def rpa_probe_density(ctx, probes, freqs, nl=None, want_tridiag=False, device_li
     if not (allow_nonconv and rc == RPA_ENOCONV):
         _check(rc, ctx)
     return dict(d=d, alpha=al, beta=be, steps=sp, stats=st.as_dict(), status=rc)
+
+
+def rpa_batch_energy(ctxs):
+    """E_c of several contexts in one call (each on its own stream and host thread)."""
+    n = len(ctxs)
+    arr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    ec = np.zeros(n)
+    st = (Stats * n)()
+    rc = load().rpa_batch_energy(n, C.cast(arr, C.c_void_p), _ptr(ec)[0], C.cast(st, C.c_void_p))
+    _check(rc, ctxs[0] if n else None)
+    return ec, [s.as_dict() for s in st]
 
 
 def rpa_interpolate(ctx, d_coarse, nd):

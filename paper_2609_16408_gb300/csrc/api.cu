@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "cocg.cuh"
@@ -465,6 +466,8 @@ static FusedBufs<T> make_fused(rpa_ctx* c) {
   fb.zchunk = fused_zchunk(c);
   fb.tiles1d = (int)tiles_of(c->nd);
   fb.first = 1;
+  fb.nact = 0;
+  fb.cd_in_smem = (sizeof(cpx<T>) * c->ngroup * kProjChunk <= 32768) ? 1 : 0;
   return fb;
 }
 
@@ -1234,6 +1237,28 @@ rpa_status rpa_probe_density(rpa_ctx* c, int count, const long long* probe, cons
   CK(cudaStreamSynchronize(c->stream));
   if (st) st->seconds_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (nonconv) return fail(c, RPA_ENOCONV, "a Sternheimer solve reached stern_maxit");
+  return RPA_OK;
+}
+
+rpa_status rpa_batch_energy(int nsys, rpa_ctx* const* sys, double* ec_out, rpa_stats* stats) {
+  if (nsys < 0 || (nsys > 0 && (!sys || !ec_out))) return RPA_EINVAL;
+  for (int i = 0; i < nsys; ++i) {
+    if (!sys[i]) return RPA_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (sys[i] == sys[j]) return fail(sys[i], RPA_EINVAL, "contexts must be distinct");
+  }
+  std::vector<rpa_status> st(nsys, RPA_OK);
+  std::vector<std::thread> th;
+  th.reserve(nsys);
+  for (int i = 0; i < nsys; ++i)
+    th.emplace_back([&, i]() {
+      cudaSetDevice(sys[i]->device);
+      st[i] = rpa_energy_density(sys[i], nullptr, nullptr, &ec_out[i],
+                                 stats ? &stats[i] : nullptr, RPA_HOST);
+    });
+  for (auto& t : th) t.join();
+  for (int i = 0; i < nsys; ++i)
+    if (st[i] != RPA_OK) return st[i];
   return RPA_OK;
 }
 

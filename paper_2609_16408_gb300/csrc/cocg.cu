@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) k_resid(CocgView<T> cv, const cpx<T>* __r
   const cpx<T>* cd = cv.cdot + (long long)s * cv.nl.ngroup * kProjChunk;
   const T* psin = cv.psi + (long long)n * nd;
   const T* ub = cv.u + (long long)b * nd;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // per-thread sums in the working precision
   const long long t0 = (long long)blockIdx.x * kTile;
   const long long t1 = min(t0 + kTile, nd);
   for (long long p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
@@ -203,11 +203,12 @@ __global__ void __launch_bounds__(256) k_resid(CocgView<T> cv, const cpx<T>* __r
       p_lo[(long long)s * nd + p] = rl;
       x_lo[(long long)s * nd + p] = mk<TL>((TL)0, (TL)0);
     }
-    acc[0] += (double)rv.re * rv.re + (double)rv.im * rv.im;
-    acc[1] += (double)bv.re * bv.re;
-    acc[2] += (double)rv.re * rv.re - (double)rv.im * rv.im;
-    acc[3] += 2.0 * (double)rv.re * rv.im;
+    a0 += rv.re * rv.re + rv.im * rv.im;
+    a1 += bv.re * bv.re;
+    a2 += rv.re * rv.re - rv.im * rv.im;
+    a3 += (T)2 * rv.re * rv.im;
   }
+  double acc[4] = {(double)a0, (double)a1, (double)a2, (double)a3};
   block_reduce<4>(acc, sh);
   if (threadIdx.x == 0) {
     double* pp = cv.part + ((long long)s * cv.tiles + blockIdx.x) * 4;

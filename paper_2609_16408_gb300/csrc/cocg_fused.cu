@@ -46,29 +46,69 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], double* sh) {
       for (int q = 0; q < NQ; ++q) v[q] += sh[w * NQ + q];
 }
 
+// Block reduction in the working precision (the partial sums of one block are short, so
+// FP32 keeps ~1e-6 relative accuracy); thread 0 returns the totals.  FP64 arithmetic is
+// avoided here because it runs at 1/58 of the FP32 rate on this GPU.
+template <typename T, int NQ>
+__device__ __forceinline__ void block_sum_t(T (&v)[NQ], T* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sh[wid * NQ + q] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < nw; ++w)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] += sh[w * NQ + q];
+}
+
 }  // namespace
 
 constexpr int kFTX = 32, kFTY = 8;
 
-// p_new at one grid point (or zero outside a Dirichlet boundary)
+// four projector values of one entry (16-byte / 32-byte aligned vector loads)
+__device__ __forceinline__ void load_chi4(const float* p, float (&c)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  c[0] = v.x;
+  c[1] = v.y;
+  c[2] = v.z;
+  c[3] = v.w;
+}
+__device__ __forceinline__ void load_chi4(const double* p, double (&c)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  c[0] = a.x;
+  c[1] = a.y;
+  c[2] = b.x;
+  c[3] = b.y;
+}
+
+// wrapped coordinate along one axis, or -1 outside a Dirichlet boundary
+__device__ __forceinline__ int axis_index(int j, int n, int bc) { return wrap_or_neg(j, n, bc); }
+
+// p_new = r + beta p_old at flat offset q (q < 0: outside a Dirichlet boundary -> 0)
 template <typename T>
-__device__ __forceinline__ cpx<T> pnew_at(const cpx<T>* __restrict__ r, const cpx<T>* __restrict__ po,
-                                          cpx<T> be, bool first, int gx, int gy, int gz,
-                                          const Stencil<T>& st) {
-  const int x = wrap_or_neg(gx, st.nx, st.bcx), y = wrap_or_neg(gy, st.ny, st.bcy),
-            z = wrap_or_neg(gz, st.nz, st.bcz);
-  if (x < 0 || y < 0 || z < 0) return mk<T>((T)0, (T)0);
-  const long long q = x + (long long)st.nx * (y + (long long)st.ny * z);
+__device__ __forceinline__ cpx<T> pnew_q(const cpx<T>* __restrict__ r, const cpx<T>* __restrict__ po,
+                                         cpx<T> be, bool first, long long q) {
+  if (q < 0) return mk<T>((T)0, (T)0);
   const cpx<T> rv = r[q];
   if (first) return rv;
   return cadd(rv, cmul(be, po[q]));
 }
 
 template <typename T, int R>
-__global__ void __launch_bounds__(kFTX * kFTY) k_dirmatvec(CocgView<T> cv, FusedBufs<T> fb) {
+__global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
+    k_dirmatvec(CocgView<T> cv, FusedBufs<T> fb) {
   const int s = cv.list ? cv.list[blockIdx.y] : blockIdx.y;
   if (cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
-  __shared__ cpx<T> pl[kFTY + 2 * R][kFTX + 2 * R];
+  constexpr int EXN = kFTX + 2 * R, EYN = kFTY + 2 * R;
+  constexpr int NHALO = EXN * EYN - kFTX * kFTY;
+  constexpr int HPT = (NHALO + kFTX * kFTY - 1) / (kFTX * kFTY);
+  __shared__ cpx<T> pl[2][EYN][EXN];
   __shared__ double sh[8 * 2];
   const Stencil<T>& st = cv.st;
   const int ntx = (st.nx + kFTX - 1) / kFTX;
@@ -80,6 +120,7 @@ __global__ void __launch_bounds__(kFTX * kFTY) k_dirmatvec(CocgView<T> cv, Fused
   const int gx = tx0 + lx, gy = ty0 + ly;
   const bool valid = gx < st.nx && gy < st.ny;
   const long long nd = cv.nd;
+  const long long plane = (long long)st.nx * st.ny;
   const cpx<T>* r = cv.r + (long long)s * nd;
   const cpx<T>* po = fb.p_in + (long long)s * nd;
   cpx<T>* pn = fb.p_out + (long long)s * nd;
@@ -89,59 +130,148 @@ __global__ void __launch_bounds__(kFTX * kFTY) k_dirmatvec(CocgView<T> cv, Fused
   const bool first = fb.first != 0;
   const int b = s / cv.ns, n = s - b * cv.ns;
   const cpx<T> sigma = mk<T>((T)cv.eps[n], (T)cv.omega[b]);
-  const cpx<T>* cd = fb.cp + (long long)s * cv.nl.ngroup * kProjChunk;
+  // this system's projector coefficients, staged in shared memory (dynamic, when they fit)
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  const int ncd = cv.nl.ngroup * kProjChunk;
+  const cpx<T>* cd = fb.cp + (long long)s * ncd;
+  if (fb.cd_in_smem) {
+    cpx<T>* scd = reinterpret_cast<cpx<T>*>(dyn_smem);
+    for (int i = threadIdx.x; i < ncd; i += blockDim.x) scd[i] = cd[i];
+    cd = scd;  // visible after the first barrier of the z loop
+  }
+  // xy offsets (fixed along z): own column and this thread's share of the halo ring
+  int own_xy;
+  {
+    const int x = axis_index(gx, st.nx, st.bcx), y = axis_index(gy, st.ny, st.bcy);
+    own_xy = (x < 0 || y < 0) ? -1 : x + st.nx * y;
+  }
+  int halo_xy[HPT], halo_slot[HPT];
+#pragma unroll
+  for (int k = 0; k < HPT; ++k) {
+    const int hi = threadIdx.x + k * kFTX * kFTY;  // index into the ring enumeration
+    halo_slot[k] = -1;
+    halo_xy[k] = -1;
+    if (hi < NHALO) {
+      // ring enumeration: R rows above, then 8 middle rows (left R, right R), then R below
+      int ey, ex;
+      if (hi < R * EXN) {
+        ey = hi / EXN;
+        ex = hi - ey * EXN;
+      } else if (hi < R * EXN + kFTY * 2 * R) {
+        const int t = hi - R * EXN;
+        ey = R + t / (2 * R);
+        const int c = t - (ey - R) * 2 * R;
+        ex = (c < R) ? c : kFTX + c;
+      } else {
+        const int t = hi - R * EXN - kFTY * 2 * R;
+        ey = R + kFTY + t / EXN;
+        ex = t - (ey - R - kFTY) * EXN;
+      }
+      halo_slot[k] = ey * EXN + ex;
+      const int x = axis_index(tx0 - R + ex, st.nx, st.bcx), y = axis_index(ty0 - R + ey, st.ny, st.bcy);
+      halo_xy[k] = (x < 0 || y < 0) ? -1 : x + st.nx * y;
+    }
+  }
+  auto zoff = [&](int z) -> long long {
+    const int zz = axis_index(z, st.nz, st.bcz);
+    return zz < 0 ? -1 : (long long)zz * plane;
+  };
+  auto colq = [&](int z) -> long long {
+    const long long zo = zoff(z);
+    return (zo < 0 || own_xy < 0) ? -1 : zo + own_xy;
+  };
   cpx<T> zq[2 * R + 1];
 #pragma unroll
-  for (int i = 0; i < 2 * R; ++i) zq[i] = pnew_at(r, po, be, first, gx, gy, z0 - R + i, st);
-  double acc2[2] = {0.0, 0.0};
-  const int ex_n = kFTX + 2 * R, ey_n = kFTY + 2 * R;
+  for (int i = 0; i < 2 * R; ++i) zq[i] = pnew_q(r, po, be, first, colq(z0 - R + i));
+  // values of the next plane, loaded one plane ahead (raw r and p, combined when stored)
+  cpx<T> nq_r, nq_p, h_r[HPT], h_p[HPT];
+  auto load_raw = [&](long long q, cpx<T>& rv, cpx<T>& pv) {
+    if (q < 0) {
+      rv = mk<T>((T)0, (T)0);
+      pv = rv;
+    } else {
+      rv = r[q];
+      pv = first ? mk<T>((T)0, (T)0) : po[q];
+    }
+  };
+  auto prefetch = [&](int z) {
+    load_raw(colq(z + R), nq_r, nq_p);
+    const long long zo = (long long)z * plane;
+#pragma unroll
+    for (int k = 0; k < HPT; ++k)
+      load_raw(halo_slot[k] >= 0 && halo_xy[k] >= 0 ? zo + halo_xy[k] : -1, h_r[k], h_p[k]);
+  };
+  auto comb = [&](cpx<T> rv, cpx<T> pv) { return first ? rv : cadd(rv, cmul(be, pv)); };
+  // projector entry range of this column's point in the next plane, loaded with the plane
+  const bool has_nl = cv.nl.ngroup > 0;
+  int ne0 = 0, ne1 = 0;
+  auto prefetch_nl = [&](int z) {
+    if (has_nl && valid) {
+      const long long q = gx + (long long)st.nx * gy + (long long)z * plane;
+      ne0 = cv.nl.p_off[q];
+      ne1 = cv.nl.p_off[q + 1];
+    }
+  };
+  if (z0 < z1) {
+    prefetch(z0);
+    prefetch_nl(z0);
+  }
+  T acc_re = 0, acc_im = 0;
   for (int z = z0; z < z1; ++z) {
-    zq[2 * R] = pnew_at(r, po, be, first, gx, gy, z + R, st);
-    // current plane into shared memory: own value, then the halo ring
-    pl[ly + R][lx + R] = zq[R];
-    for (int e = threadIdx.x; e < ex_n * ey_n; e += blockDim.x) {
-      const int ey = e / ex_n, ex = e - ey * ex_n;
-      if (ey >= R && ey < R + kFTY && ex >= R && ex < R + kFTX) continue;
-      pl[ey][ex] = pnew_at(r, po, be, first, tx0 - R + ex, ty0 - R + ey, z, st);
+    const int buf = (z - z0) & 1;
+    zq[2 * R] = comb(nq_r, nq_p);
+    pl[buf][ly + R][lx + R] = zq[R];
+#pragma unroll
+    for (int k = 0; k < HPT; ++k)
+      if (halo_slot[k] >= 0) (&pl[buf][0][0])[halo_slot[k]] = comb(h_r[k], h_p[k]);
+    const int e0 = ne0, e1 = ne1;
+    if (z + 1 < z1) {  // in flight while this plane is computed
+      prefetch(z + 1);
+      prefetch_nl(z + 1);
     }
     __syncthreads();
     if (valid) {
-      const long long q = gx + (long long)st.nx * (gy + (long long)st.ny * z);
+      const long long q = gx + (long long)st.nx * gy + (long long)z * plane;
       const cpx<T> c = zq[R];
       const T dg = st.c0 + cv.vloc[q];
       cpx<T> a = mk<T>(dg * c.re - (sigma.re * c.re - sigma.im * c.im),
                        dg * c.im - (sigma.re * c.im + sigma.im * c.re));
 #pragma unroll
       for (int m = 1; m <= R; ++m) {
-        a = caxpy_r(a, st.cx[m], cadd(pl[ly + R][lx + R - m], pl[ly + R][lx + R + m]));
-        a = caxpy_r(a, st.cy[m], cadd(pl[ly + R - m][lx + R], pl[ly + R + m][lx + R]));
+        a = caxpy_r(a, st.cx[m], cadd(pl[buf][ly + R][lx + R - m], pl[buf][ly + R][lx + R + m]));
+        a = caxpy_r(a, st.cy[m], cadd(pl[buf][ly + R - m][lx + R], pl[buf][ly + R + m][lx + R]));
         a = caxpy_r(a, st.cz[m], cadd(zq[R - m], zq[R + m]));
       }
-      if (cv.nl.ngroup > 0) {
-        const int e0 = cv.nl.p_off[q], e1 = cv.nl.p_off[q + 1];
-        for (int e = e0; e < e1; ++e) {
-          const int g = cv.nl.p_grp[e];
-          const T* ch = cv.nl.p_chi + (long long)e * kProjChunk;
-          const cpx<T>* cg = cd + (long long)g * kProjChunk;
+      for (int e = e0; e < e1; e += 2) {  // two entries in flight per step
+        const bool two = e + 1 < e1;
+        const int g0 = cv.nl.p_grp[e];
+        const int g1 = two ? cv.nl.p_grp[e + 1] : g0;
+        T c0[kProjChunk], c1[kProjChunk];
+        load_chi4(cv.nl.p_chi + (long long)e * kProjChunk, c0);
+        if (two) load_chi4(cv.nl.p_chi + (long long)(e + 1) * kProjChunk, c1);
+        const cpx<T>* cg0 = cd + (long long)g0 * kProjChunk;
+        const cpx<T>* cg1 = cd + (long long)g1 * kProjChunk;
 #pragma unroll
-          for (int l = 0; l < kProjChunk; ++l) a = caxpy_r(a, ch[l], cg[l]);
+        for (int l = 0; l < kProjChunk; ++l) {
+          a = caxpy_r(a, c0[l], cg0[l]);
+          if (two) a = caxpy_r(a, c1[l], cg1[l]);
         }
       }
       w[q] = a;
       pn[q] = c;
-      acc2[0] += (double)c.re * a.re - (double)c.im * a.im;
-      acc2[1] += (double)c.re * a.im + (double)c.im * a.re;
+      acc_re += c.re * a.re - c.im * a.im;
+      acc_im += c.re * a.im + c.im * a.re;
     }
-    __syncthreads();
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) zq[i] = zq[i + 1];
   }
-  block_sum<2>(acc2, sh);
+  T acc2[2] = {acc_re, acc_im};
+  block_sum_t<T, 2>(acc2, reinterpret_cast<T*>(sh));
   if (threadIdx.x == 0) {
     const int pid = blockIdx.x + gridDim.x * blockIdx.z;
     double* pp = cv.part + ((long long)s * cv.tiles + pid) * 4;
-    pp[0] = acc2[0];
-    pp[1] = acc2[1];
+    pp[0] = (double)acc2[0];
+    pp[1] = (double)acc2[1];
   }
 }
 
@@ -160,20 +290,39 @@ __global__ void __launch_bounds__(256) k_update_dots(CocgView<T> cv, FusedBufs<T
   const double* sd = cv.sysd + (long long)s * kSysD;
   const cpx<T> al = mk<T>((T)sd[kAlpha], (T)sd[kAlpha + 1]);
   const bool nl = cv.nl.ngroup > 0;
-  double acc[3] = {0.0, 0.0, 0.0};
+  T a0 = 0, a1 = 0, a2 = 0;
   const long long t0 = (long long)blockIdx.x * kTile;
   const long long t1 = min(t0 + kTile, nd);
-  for (long long p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
-    const long long q = (long long)s * nd + p;
-    const cpx<T> pv = fb.p_out[q], wv = cv.w[q];
-    cv.x[q] = cadd(cv.x[q], cmul(al, pv));
-    const cpx<T> rv = csub(cv.r[q], cmul(al, wv));
-    cv.r[q] = rv;
-    if (nl) sr[p - t0] = rv;
-    acc[0] += (double)rv.re * rv.re + (double)rv.im * rv.im;
-    acc[1] += (double)rv.re * rv.re - (double)rv.im * rv.im;
-    acc[2] += 2.0 * (double)rv.re * rv.im;
+  const cpx<T>* __restrict__ pp_ = fb.p_out + (long long)s * nd;
+  const cpx<T>* __restrict__ ww_ = cv.w + (long long)s * nd;
+  cpx<T>* __restrict__ xx_ = cv.x + (long long)s * nd;
+  cpx<T>* __restrict__ rr_ = cv.r + (long long)s * nd;
+  constexpr int U = kTile / 256;  // points per thread, all loads issued before any store
+  cpx<T> pv[U], wv[U], xv[U], rv0[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const long long p = t0 + threadIdx.x + u * 256;
+    if (p < t1) {
+      pv[u] = pp_[p];
+      wv[u] = ww_[p];
+      xv[u] = xx_[p];
+      rv0[u] = rr_[p];
+    }
   }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const long long p = t0 + threadIdx.x + u * 256;
+    if (p < t1) {
+      xx_[p] = cadd(xv[u], cmul(al, pv[u]));
+      const cpx<T> rv = csub(rv0[u], cmul(al, wv[u]));
+      rr_[p] = rv;
+      if (nl) sr[p - t0] = rv;
+      a0 += rv.re * rv.re + rv.im * rv.im;
+      a1 += rv.re * rv.re - rv.im * rv.im;
+      a2 += (T)2 * rv.re * rv.im;
+    }
+  }
+  T acc[3] = {a0, a1, a2};
   if (nl) {
     __syncthreads();
     cpx<T>* cr = fb.cr + (long long)s * cv.nl.ngroup * kProjChunk;
@@ -194,10 +343,11 @@ __global__ void __launch_bounds__(256) k_update_dots(CocgView<T> cv, FusedBufs<T
           a[2 * l + 1] += ch[l] * rv.im;
         }
       }
+      // butterfly reduction: every lane ends with the full sums
 #pragma unroll
       for (int i = 0; i < 2 * kProjChunk; ++i)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a[i] += __shfl_down_sync(0xffffffffu, a[i], o);
+        for (int o = 16; o > 0; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
       if (lane < kProjChunk) {
         T re = a[0], im = a[1];
 #pragma unroll
@@ -212,12 +362,12 @@ __global__ void __launch_bounds__(256) k_update_dots(CocgView<T> cv, FusedBufs<T
       }
     }
   }
-  block_sum<3>(acc, sh);
+  block_sum_t<T, 3>(acc, reinterpret_cast<T*>(sh));
   if (threadIdx.x == 0) {
     double* pp = cv.part + ((long long)s * cv.tiles + blockIdx.x) * 4;
-    pp[0] = acc[0];
-    pp[2] = acc[1];
-    pp[3] = acc[2];
+    pp[0] = (double)acc[0];
+    pp[2] = (double)acc[1];
+    pp[3] = (double)acc[2];
   }
 }
 
@@ -246,7 +396,8 @@ __global__ void k_proj_next(int nsys, int ngroup, const double* __restrict__ sys
 template <typename T, int R>
 static void launch_dirmatvec(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s) {
   dim3 grid(fb.ntiles_xy, fb.nact, fb.nzchunk);
-  k_dirmatvec<T, R><<<grid, kFTX * kFTY, 0, s>>>(cv, fb);
+  const size_t dyn = fb.cd_in_smem ? sizeof(cpx<T>) * cv.nl.ngroup * kProjChunk : 0;
+  k_dirmatvec<T, R><<<grid, kFTX * kFTY, dyn, s>>>(cv, fb);
 }
 
 template <typename T>

@@ -15,6 +15,7 @@ struct FusedBufs {
   const int* tile_ranges;  // (group, first entry, end entry) of group-major entries in a tile
   int ntiles_xy, nzchunk, zchunk, tiles1d, first;
   int nact;                // launched systems: the first nact entries of CocgView::list
+  int cd_in_smem;          // stage the projector coefficients of a system in shared memory
 };
 
 template <typename T>
