@@ -204,6 +204,29 @@ rpa_status rpa_chi0(rpa_ctx *ctx, int count, const double *omega, const double *
 rpa_status rpa_galerkin(rpa_ctx *ctx, int count, const double *omega, const double *u,
                         double *x0, int where);
 
+/* Galerkin initial guesses (as rpa_galerkin in the FP64 form) for callers that cannot
+ * allocate device memory themselves -- for instance code running under another framework's
+ * memory pool, or a path that must avoid cudaMalloc/cudaFree because they synchronise the
+ * whole device.  The paper has no counterpart; this is a service of the library.
+ *   All pointers are DEVICE pointers of the current device: psi (ns x nd, state-major,
+ *   dV sum psi^2 = 1), eps (ns), omega (count), u (count x nd real), x0 (count x ns x nd
+ *   complex, interleaved) -- the caller owns and allocates them.  dV: volume element.
+ *   Work is queued on cuda_stream (NULL: the legacy default stream) and the call returns
+ *   without synchronising; read x0 after synchronising that stream.
+ *   Scratch: a fixed 8 MiB file-scope device array (held by every GPU that loads the library
+ *   until exit); needs ceil(nd/4096) (clamped to 1..256) x ns^2 x 8 bytes (rounded up to a
+ *   multiple of 256) + ns^2 x 16 bytes, e.g.
+ *   35 x 128^2 x 8 + 128^2 x 16 = 4.85 MB for a 52^3 grid with 128 states.  Larger sizes are
+ *   rejected with RPA_EINVAL before any work is queued.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *   make that first call before any stream capture.  The call allocates nothing (no
+ *   cudaMalloc, no cudaFree).  Every call shares the scratch array and leaves its contents
+ *   behind; calls whose work overlaps on the GPU (different streams, or host threads
+ *   without ordering) race on it and must be serialised by the caller. */
+rpa_status rpa_galerkin_noalloc(long long nd, int ns, const double *psi, const double *eps,
+                                double dV, int count, const double *omega, const double *u,
+                                double *x0, void *cuda_stream);
+
 /* d_i = [f(T_i)]_{11} for count symmetric tridiagonals of order k (alpha: count x k,
  * beta: count x k with beta[i*k + k-1] ignored); host arrays; solved on the device. */
 rpa_status rpa_tridiag_f11(int count, int k, const double *alpha, const double *beta,

@@ -142,6 +142,7 @@ def _declare(lib):
         "rpa_tridiag_f11": ([I, I, P, P, I, P], I),
         "rpa_galerkin": ([P, I, P, P, P, I], I),
         "rpa_batch_energy": ([I, P, P, P], I),
+        "rpa_galerkin_noalloc": ([LL, I, P, P, D, I, P, P, P, P], I),
         "rpa_status_string": ([I], C.c_char_p),
         "rpa_last_error": ([P], C.c_char_p),
         "rpa_kernel_launches": ([P], LL),
@@ -395,6 +396,35 @@ def rpa_galerkin(ctx, omega, u, ns):
     x0 = np.empty((u.shape[0], ns, u.shape[1]), dtype=np.complex128)
     _check(load().rpa_galerkin(ctx, u.shape[0], _ptr(om)[0], _ptr(u)[0], _ptr(x0)[0], RPA_HOST),
            ctx)
+    return x0
+
+
+# Scratch size of rpa_galerkin_noalloc (bytes); see include/rpa.h.
+NOALLOC_SCRATCH_BYTES = 8 << 20
+
+
+def rpa_galerkin_noalloc(psi, eps, dV, omega, u, x0, stream=None):
+    """FP64 Galerkin guesses for callers that cannot allocate device memory.
+
+    All arguments are CUDA tensors owned by the caller: psi (ns, nd) float64, eps (ns,),
+    omega (count,), u (count, nd) float64, x0 (count, ns, nd) complex128 output.  Work is
+    queued on `stream` (a torch.cuda.Stream or None for the current stream) without
+    synchronising.  Uses a fixed 8 MiB device scratch array inside the library; sizes beyond
+    it raise RpaError(RPA_EINVAL)."""
+    import torch
+    ns, nd = int(psi.shape[0]), int(psi.shape[1])
+    count = int(u.shape[0]) if u.dim() == 2 else 1
+    nchunk = min(256, max(1, (nd + 4095) // 4096))
+    need = ((nchunk * ns * ns * 8 + 255) // 256) * 256 + ns * ns * 16
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = load().rpa_galerkin_noalloc(nd, ns, C.c_void_p(psi.data_ptr()),
+                                     C.c_void_p(eps.data_ptr()), float(dV), count,
+                                     C.c_void_p(omega.data_ptr()), C.c_void_p(u.data_ptr()),
+                                     C.c_void_p(x0.data_ptr()), C.c_void_p(st.cuda_stream))
+    if rc == RPA_EINVAL and need > NOALLOC_SCRATCH_BYTES:
+        raise RpaError(rc, f"rpa_galerkin_noalloc: needs {need} bytes of scratch, more than "
+                           f"the {NOALLOC_SCRATCH_BYTES} bytes it holds")
+    _check(rc)
     return x0
 
 
