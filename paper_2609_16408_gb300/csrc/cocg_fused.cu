@@ -87,72 +87,64 @@ __device__ __forceinline__ void load_chi4(const double* p, double (&c)[4]) {
   c[3] = b.y;
 }
 
-// wrapped coordinate along one axis, or -1 outside a Dirichlet boundary
-__device__ __forceinline__ int axis_index(int j, int n, int bc) { return wrap_or_neg(j, n, bc); }
-
-// p_new = r + beta p_old at flat offset q (q < 0: outside a Dirichlet boundary -> 0)
-template <typename T>
-__device__ __forceinline__ cpx<T> pnew_q(const cpx<T>* __restrict__ r, const cpx<T>* __restrict__ po,
-                                         cpx<T> be, bool first, long long q) {
-  if (q < 0) return mk<T>((T)0, (T)0);
-  const cpx<T> rv = r[q];
-  if (first) return rv;
-  return cadd(rv, cmul(be, po[q]));
-}
-
-template <typename T, int R>
+// Direction update + H apply, 2.5-D blocked (see the file comment).  All offsets inside a
+// system are 32-bit (N_d < 2^31); stencil neighbours are read from shared memory at
+// compile-time offsets from a per-thread base; FIRST marks the first iteration of a solve
+// (p_k = r_k, no previous direction).  The projector coefficients of the system are in
+// shared memory when SMEM_CD, else read through the read-only path.
+template <typename T, int R, bool FIRST, bool SMEM_CD>
 __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
     k_dirmatvec(CocgView<T> cv, FusedBufs<T> fb) {
   const int s = cv.list ? cv.list[blockIdx.y] : blockIdx.y;
   if (cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
   constexpr int EXN = kFTX + 2 * R, EYN = kFTY + 2 * R;
-  constexpr int NHALO = EXN * EYN - kFTX * kFTY;
+  constexpr int PLN = EXN * EYN;
+  constexpr int NHALO = PLN - kFTX * kFTY;
   constexpr int HPT = (NHALO + kFTX * kFTY - 1) / (kFTX * kFTY);
-  __shared__ cpx<T> pl[2][EYN][EXN];
-  __shared__ double sh[8 * 2];
+  __shared__ cpx<T> pl[2 * PLN];
+  __shared__ T sh[8 * 2];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   const Stencil<T>& st = cv.st;
-  const int ntx = (st.nx + kFTX - 1) / kFTX;
-  const int tile = blockIdx.x;
-  const int tx0 = (tile % ntx) * kFTX, ty0 = (tile / ntx) * kFTY;
-  const int zc = blockIdx.z;
-  const int z0 = zc * fb.zchunk, z1 = min(z0 + fb.zchunk, st.nz);
+  const int nx = st.nx, ny = st.ny, nz = st.nz;
+  const int plane = nx * ny;
+  const int ntx = (nx + kFTX - 1) / kFTX;
+  const int tx0 = (blockIdx.x % ntx) * kFTX, ty0 = (blockIdx.x / ntx) * kFTY;
+  const int z0 = blockIdx.z * fb.zchunk, z1 = min(z0 + fb.zchunk, nz);
   const int lx = threadIdx.x & (kFTX - 1), ly = threadIdx.x / kFTX;
   const int gx = tx0 + lx, gy = ty0 + ly;
-  const bool valid = gx < st.nx && gy < st.ny;
-  const long long nd = cv.nd;
-  const long long plane = (long long)st.nx * st.ny;
-  const cpx<T>* r = cv.r + (long long)s * nd;
-  const cpx<T>* po = fb.p_in + (long long)s * nd;
-  cpx<T>* pn = fb.p_out + (long long)s * nd;
-  cpx<T>* w = cv.w + (long long)s * nd;
+  const bool valid = gx < nx && gy < ny;
+  const long long sbase = (long long)s * cv.nd;
+  const cpx<T>* __restrict__ r = cv.r + sbase;
+  const cpx<T>* __restrict__ po = fb.p_in + sbase;
+  cpx<T>* __restrict__ pn = fb.p_out + sbase;
+  cpx<T>* __restrict__ w = cv.w + sbase;
+  const T* __restrict__ vloc = cv.vloc;
   const double* sd = cv.sysd + (long long)s * kSysD;
   const cpx<T> be = mk<T>((T)sd[kBeta], (T)sd[kBeta + 1]);
-  const bool first = fb.first != 0;
   const int b = s / cv.ns, n = s - b * cv.ns;
   const cpx<T> sigma = mk<T>((T)cv.eps[n], (T)cv.omega[b]);
-  // this system's projector coefficients, staged in shared memory (dynamic, when they fit)
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int ncd = cv.nl.ngroup * kProjChunk;
   const cpx<T>* cd = fb.cp + (long long)s * ncd;
-  if (fb.cd_in_smem) {
+  if (SMEM_CD) {
     cpx<T>* scd = reinterpret_cast<cpx<T>*>(dyn_smem);
     for (int i = threadIdx.x; i < ncd; i += blockDim.x) scd[i] = cd[i];
-    cd = scd;  // visible after the first barrier of the z loop
+    cd = scd;  // read after the first barrier of the z loop
   }
-  // xy offsets (fixed along z): own column and this thread's share of the halo ring
+  // xy offsets (fixed along z) of the own column and of this thread's halo elements
   int own_xy;
   {
-    const int x = axis_index(gx, st.nx, st.bcx), y = axis_index(gy, st.ny, st.bcy);
-    own_xy = (x < 0 || y < 0) ? -1 : x + st.nx * y;
+    const int x = wrap_or_neg(gx, nx, st.bcx), y = wrap_or_neg(gy, ny, st.bcy);
+    own_xy = (x < 0 || y < 0) ? -1 : x + nx * y;
   }
-  int halo_xy[HPT], halo_slot[HPT];
+  int halo_xy[HPT];
+  cpx<T>* halo_s[HPT];
 #pragma unroll
   for (int k = 0; k < HPT; ++k) {
     const int hi = threadIdx.x + k * kFTX * kFTY;  // index into the ring enumeration
-    halo_slot[k] = -1;
+    halo_s[k] = nullptr;
     halo_xy[k] = -1;
     if (hi < NHALO) {
-      // ring enumeration: R rows above, then 8 middle rows (left R, right R), then R below
+      // ring: R rows above, then kFTY middle rows (left R, right R), then R rows below
       int ey, ex;
       if (hi < R * EXN) {
         ey = hi / EXN;
@@ -167,94 +159,94 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
         ey = R + kFTY + t / EXN;
         ex = t - (ey - R - kFTY) * EXN;
       }
-      halo_slot[k] = ey * EXN + ex;
-      const int x = axis_index(tx0 - R + ex, st.nx, st.bcx), y = axis_index(ty0 - R + ey, st.ny, st.bcy);
-      halo_xy[k] = (x < 0 || y < 0) ? -1 : x + st.nx * y;
+      halo_s[k] = pl + ey * EXN + ex;
+      const int x = wrap_or_neg(tx0 - R + ex, nx, st.bcx), y = wrap_or_neg(ty0 - R + ey, ny, st.bcy);
+      halo_xy[k] = (x < 0 || y < 0) ? -1 : x + nx * y;
     }
   }
-  auto zoff = [&](int z) -> long long {
-    const int zz = axis_index(z, st.nz, st.bcz);
-    return zz < 0 ? -1 : (long long)zz * plane;
+  cpx<T>* const own_s = pl + (ly + R) * EXN + (lx + R);
+  auto zoff = [&](int z) -> int {
+    const int zz = wrap_or_neg(z, nz, st.bcz);
+    return zz < 0 ? -1 : zz * plane;
   };
-  auto colq = [&](int z) -> long long {
-    const long long zo = zoff(z);
-    return (zo < 0 || own_xy < 0) ? -1 : zo + own_xy;
-  };
-  cpx<T> zq[2 * R + 1];
-#pragma unroll
-  for (int i = 0; i < 2 * R; ++i) zq[i] = pnew_q(r, po, be, first, colq(z0 - R + i));
-  // values of the next plane, loaded one plane ahead (raw r and p, combined when stored)
-  cpx<T> nq_r, nq_p, h_r[HPT], h_p[HPT];
-  auto load_raw = [&](long long q, cpx<T>& rv, cpx<T>& pv) {
+  auto ld = [&](int q, cpx<T>& rv, cpx<T>& pv) {
     if (q < 0) {
       rv = mk<T>((T)0, (T)0);
       pv = rv;
     } else {
       rv = r[q];
-      pv = first ? mk<T>((T)0, (T)0) : po[q];
+      if (!FIRST) pv = po[q];
     }
   };
-  auto prefetch = [&](int z) {
-    load_raw(colq(z + R), nq_r, nq_p);
-    const long long zo = (long long)z * plane;
+  auto comb = [&](const cpx<T>& rv, const cpx<T>& pv) -> cpx<T> {
+    if (FIRST) return rv;
+    return cadd(rv, cmul(be, pv));
+  };
+  cpx<T> zq[2 * R + 1];
 #pragma unroll
-    for (int k = 0; k < HPT; ++k)
-      load_raw(halo_slot[k] >= 0 && halo_xy[k] >= 0 ? zo + halo_xy[k] : -1, h_r[k], h_p[k]);
-  };
-  auto comb = [&](cpx<T> rv, cpx<T> pv) { return first ? rv : cadd(rv, cmul(be, pv)); };
-  // projector entry range of this column's point in the next plane, loaded with the plane
-  const bool has_nl = cv.nl.ngroup > 0;
-  int ne0 = 0, ne1 = 0;
-  auto prefetch_nl = [&](int z) {
-    if (has_nl && valid) {
-      const long long q = gx + (long long)st.nx * gy + (long long)z * plane;
-      ne0 = cv.nl.p_off[q];
-      ne1 = cv.nl.p_off[q + 1];
-    }
-  };
-  if (z0 < z1) {
-    prefetch(z0);
-    prefetch_nl(z0);
+  for (int i = 0; i < 2 * R; ++i) {
+    const int zo = zoff(z0 - R + i);
+    cpx<T> rv, pv;
+    ld((zo < 0 || own_xy < 0) ? -1 : zo + own_xy, rv, pv);
+    zq[i] = comb(rv, pv);
   }
+  cpx<T> nq_r, nq_p, h_r[HPT], h_p[HPT];
+  const bool has_nl = cv.nl.ngroup > 0;
+  const int* __restrict__ p_off = cv.nl.p_off;
+  const int* __restrict__ p_grp = cv.nl.p_grp;
+  const T* __restrict__ p_chi = cv.nl.p_chi;
+  int ne0 = 0, ne1 = 0;
+  auto prefetch = [&](int z) {
+    const int zo = zoff(z + R);
+    ld((zo < 0 || own_xy < 0) ? -1 : zo + own_xy, nq_r, nq_p);
+    const int zp = z * plane;
+#pragma unroll
+    for (int k = 0; k < HPT; ++k) ld(halo_xy[k] < 0 ? -1 : zp + halo_xy[k], h_r[k], h_p[k]);
+    if (has_nl && valid) {
+      const int q = own_xy + zp;
+      ne0 = p_off[q];
+      ne1 = p_off[q + 1];
+    }
+  };
+  if (z0 < z1) prefetch(z0);
   T acc_re = 0, acc_im = 0;
+  const T c0 = st.c0;
   for (int z = z0; z < z1; ++z) {
-    const int buf = (z - z0) & 1;
+    const int bo = ((z - z0) & 1) * PLN;
     zq[2 * R] = comb(nq_r, nq_p);
-    pl[buf][ly + R][lx + R] = zq[R];
+    own_s[bo] = zq[R];
 #pragma unroll
     for (int k = 0; k < HPT; ++k)
-      if (halo_slot[k] >= 0) (&pl[buf][0][0])[halo_slot[k]] = comb(h_r[k], h_p[k]);
+      if (halo_s[k]) halo_s[k][bo] = comb(h_r[k], h_p[k]);
     const int e0 = ne0, e1 = ne1;
-    if (z + 1 < z1) {  // in flight while this plane is computed
-      prefetch(z + 1);
-      prefetch_nl(z + 1);
-    }
+    if (z + 1 < z1) prefetch(z + 1);  // in flight while this plane is computed
     __syncthreads();
     if (valid) {
-      const long long q = gx + (long long)st.nx * gy + (long long)z * plane;
+      const int q = own_xy + z * plane;
       const cpx<T> c = zq[R];
-      const T dg = st.c0 + cv.vloc[q];
+      const cpx<T>* cs = own_s + bo;
+      const T dg = c0 + vloc[q];
       cpx<T> a = mk<T>(dg * c.re - (sigma.re * c.re - sigma.im * c.im),
                        dg * c.im - (sigma.re * c.im + sigma.im * c.re));
 #pragma unroll
       for (int m = 1; m <= R; ++m) {
-        a = caxpy_r(a, st.cx[m], cadd(pl[buf][ly + R][lx + R - m], pl[buf][ly + R][lx + R + m]));
-        a = caxpy_r(a, st.cy[m], cadd(pl[buf][ly + R - m][lx + R], pl[buf][ly + R + m][lx + R]));
+        a = caxpy_r(a, st.cx[m], cadd(cs[-m], cs[m]));
+        a = caxpy_r(a, st.cy[m], cadd(cs[-m * EXN], cs[m * EXN]));
         a = caxpy_r(a, st.cz[m], cadd(zq[R - m], zq[R + m]));
       }
-      for (int e = e0; e < e1; e += 2) {  // two entries in flight per step
+      for (int e = e0; e < e1; e += 2) {  // two projector entries in flight per step
         const bool two = e + 1 < e1;
-        const int g0 = cv.nl.p_grp[e];
-        const int g1 = two ? cv.nl.p_grp[e + 1] : g0;
-        T c0[kProjChunk], c1[kProjChunk];
-        load_chi4(cv.nl.p_chi + (long long)e * kProjChunk, c0);
-        if (two) load_chi4(cv.nl.p_chi + (long long)(e + 1) * kProjChunk, c1);
-        const cpx<T>* cg0 = cd + (long long)g0 * kProjChunk;
-        const cpx<T>* cg1 = cd + (long long)g1 * kProjChunk;
+        const int g0 = p_grp[e];
+        const int g1 = two ? p_grp[e + 1] : g0;
+        T ch0[kProjChunk], ch1[kProjChunk];
+        load_chi4(p_chi + kProjChunk * e, ch0);
+        if (two) load_chi4(p_chi + kProjChunk * (e + 1), ch1);
+        const cpx<T>* cg0 = cd + kProjChunk * g0;
+        const cpx<T>* cg1 = cd + kProjChunk * g1;
 #pragma unroll
         for (int l = 0; l < kProjChunk; ++l) {
-          a = caxpy_r(a, c0[l], cg0[l]);
-          if (two) a = caxpy_r(a, c1[l], cg1[l]);
+          a = caxpy_r(a, ch0[l], cg0[l]);
+          if (two) a = caxpy_r(a, ch1[l], cg1[l]);
         }
       }
       w[q] = a;
@@ -266,7 +258,7 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
     for (int i = 0; i < 2 * R; ++i) zq[i] = zq[i + 1];
   }
   T acc2[2] = {acc_re, acc_im};
-  block_sum_t<T, 2>(acc2, reinterpret_cast<T*>(sh));
+  block_sum_t<T, 2>(acc2, sh);
   if (threadIdx.x == 0) {
     const int pid = blockIdx.x + gridDim.x * blockIdx.z;
     double* pp = cv.part + ((long long)s * cv.tiles + pid) * 4;
@@ -395,16 +387,23 @@ __global__ void k_proj_next(int nsys, int ngroup, const double* __restrict__ sys
 // -------------------------------------------------------------------------------------------
 template <typename T, int R>
 static void launch_dirmatvec(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s) {
+  const size_t cdb = fb.cd_in_smem ? sizeof(cpx<T>) * cv.nl.ngroup * kProjChunk : 0;
   dim3 grid(fb.ntiles_xy, fb.nact, fb.nzchunk);
-  const size_t dyn = fb.cd_in_smem ? sizeof(cpx<T>) * cv.nl.ngroup * kProjChunk : 0;
-  k_dirmatvec<T, R><<<grid, kFTX * kFTY, dyn, s>>>(cv, fb);
+  if (fb.first) {
+    if (fb.cd_in_smem)
+      k_dirmatvec<T, R, true, true><<<grid, kFTX * kFTY, cdb, s>>>(cv, fb);
+    else
+      k_dirmatvec<T, R, true, false><<<grid, kFTX * kFTY, 0, s>>>(cv, fb);
+  } else {
+    if (fb.cd_in_smem)
+      k_dirmatvec<T, R, false, true><<<grid, kFTX * kFTY, cdb, s>>>(cv, fb);
+    else
+      k_dirmatvec<T, R, false, false><<<grid, kFTX * kFTY, 0, s>>>(cv, fb);
+  }
 }
 
 template <typename T>
-cudaError_t fused_iteration(const CocgView<T>& cv, const FusedBufs<T>& fb, double tol, int maxit,
-                            cudaStream_t s, cudaEvent_t* ev) {
-  if (ev) cudaEventRecord(ev[0], s);
-  if (ev) cudaEventRecord(ev[1], s);
+cudaError_t launch_dirmatvec_only(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s) {
   switch (cv.st.R) {
     case 1: launch_dirmatvec<T, 1>(cv, fb, s); break;
     case 2: launch_dirmatvec<T, 2>(cv, fb, s); break;
@@ -414,6 +413,23 @@ cudaError_t fused_iteration(const CocgView<T>& cv, const FusedBufs<T>& fb, doubl
     case 6: launch_dirmatvec<T, 6>(cv, fb, s); break;
     case 7: launch_dirmatvec<T, 7>(cv, fb, s); break;
     default: launch_dirmatvec<T, 8>(cv, fb, s); break;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_dirmatvec_only<float>(const CocgView<float>&, const FusedBufs<float>&,
+                                                  cudaStream_t);
+template cudaError_t launch_dirmatvec_only<double>(const CocgView<double>&,
+                                                   const FusedBufs<double>&, cudaStream_t);
+
+template <typename T>
+cudaError_t fused_iteration(const CocgView<T>& cv, const FusedBufs<T>& fb, double tol, int maxit,
+                            cudaStream_t s, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], s);
+  if (ev) cudaEventRecord(ev[1], s);
+  {
+    cudaError_t e0 = launch_dirmatvec_only<T>(cv, fb, s);
+    if (e0 != cudaSuccess) return e0;
   }
   if (ev) cudaEventRecord(ev[2], s);
   cudaError_t e = cocg_scalars(fb.nact, fb.ntiles_xy * fb.nzchunk, cv.part, cv.sysd, cv.sysi, 1,
@@ -433,7 +449,7 @@ cudaError_t fused_iteration(const CocgView<T>& cv, const FusedBufs<T>& fb, doubl
   }
   if (ev) cudaEventRecord(ev[5], s);
   if (ev) cudaEventRecord(ev[6], s);
-  note_launch(2);
+  note_launch(1);
   return cudaGetLastError();
 }
 

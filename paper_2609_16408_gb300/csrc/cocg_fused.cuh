@@ -18,6 +18,10 @@ struct FusedBufs {
   int cd_in_smem;          // stage the projector coefficients of a system in shared memory
 };
 
+// the direction + H-apply kernel alone (used by the tile autotuner)
+template <typename T>
+cudaError_t launch_dirmatvec_only(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s);
+
 template <typename T>
 cudaError_t fused_iteration(const CocgView<T>& cv, const FusedBufs<T>& fb, double tol, int maxit,
                             cudaStream_t s, cudaEvent_t* ev = nullptr);

@@ -10,5 +10,5 @@ CUDA library: both receive the arrays this package produces.
 """
 from .systems import (  # noqa: F401
     PERIODIC, DIRICHLET, System, ProjectorGroup, toy_system, si_like_system,
-    cluster_system, gaussian_system, named_system, probe_sample,
+    cluster_system, gaussian_system, named_system, probe_sample, lih_like_system,
 )

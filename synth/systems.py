@@ -496,6 +496,41 @@ def si_like_system(ncell=(1, 1, 1), a=10.26, pts_per_cell=26, ns=None, seed=1,
                            seed=seed, min_gap=min_gap, _positions_fn=pos, **kw)
 
 
+def rocksalt_sites(a: float, ncell=(1, 1, 1)):
+    """Cation and anion sites of a rock-salt cell (4 + 4 per cubic cell)."""
+    fcc = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
+    cat, an = [], []
+    for i in range(ncell[0]):
+        for j in range(ncell[1]):
+            for k in range(ncell[2]):
+                off = np.array([i, j, k])
+                cat.append((fcc + off) * a)
+                an.append((fcc + np.array([0.5, 0, 0]) + off) * a)
+    return np.concatenate(cat), np.concatenate(an)
+
+
+def lih_like_system(ncell=(2, 2, 2), a=7.71, pts_per_cell=16, seed=7, fd_radius=6, **kw):
+    """Perturbed rock-salt LiH-like cell (no projectors): a deep narrow well on each Li site
+    (D ~ U[4.5, 5.5] Ha, sigma = 0.5 bohr) and a shallower wider well on each H site
+    (D ~ U[1.3, 1.7] Ha, sigma = 0.8 bohr) bind one state each, so the occupied set is two
+    states per LiH unit (four electrons, as in the paper's LiH systems) below a large gap.
+    h = a / pts_per_cell (0.48 bohr at the default, cf. h ~ 0.47 in the LiH scaling runs)."""
+    n = tuple(pts_per_cell * c for c in ncell)
+    L = tuple(a * c for c in ncell)
+    li, h = rocksalt_sites(a, ncell)
+    nunit = len(li)
+    delta = 0.1 * (a / 2.0)
+
+    def pos(rng):
+        c = np.concatenate([li, h]) + delta * rng.uniform(-0.5, 0.5, size=(2 * nunit, 3))
+        d = np.concatenate([rng.uniform(4.5, 5.5, size=nunit), rng.uniform(1.3, 1.7, size=nunit)])
+        sg = np.concatenate([np.full(nunit, 0.5), np.full(nunit, 0.8)])
+        return c, d, sg
+    name = f"lih{nunit}_{'x'.join(map(str, n))}"
+    return gaussian_system(name, n, L, (PERIODIC,) * 3, None, None, None, 2 * nunit,
+                           fd_radius=fd_radius, seed=seed, _positions_fn=pos, **kw)
+
+
 def cluster_system(natom=12, box=16.0, n=40, ns=24, seed=6, fd_radius=6, **kw):
     """Isolated Gaussian-well cluster with zero Dirichlet walls on all axes."""
     def pos(rng):
@@ -509,13 +544,22 @@ def cluster_system(natom=12, box=16.0, n=40, ns=24, seed=6, fd_radius=6, **kw):
 
 
 def named_system(name: str, **kw) -> System:
-    """The workloads by name: toy (12^3), si8 (26^3), si64 (52^3)."""
+    """The workloads by name: toy (12^3), si8 (26^3), si64 (52^3), si64p (40^3), lih4 (16^3),
+    lih32 (32^3), cluster12 (40^3 Dirichlet)."""
     if name == "toy":
         return toy_system(**kw)
+    if name == "lih4":
+        return lih_like_system((1, 1, 1), **kw)
+    if name == "lih32":
+        return lih_like_system((2, 2, 2), **kw)
+    if name == "cluster12":
+        return cluster_system(**kw)
     if name == "si8":
         return si_like_system((1, 1, 1), seed=1, **kw)
     if name == "si64":
         return si_like_system((2, 2, 2), seed=2, **kw)
+    if name == "si64p":
+        return si_like_system((2, 2, 2), pts_per_cell=20, seed=2, **kw)
     raise KeyError(name)
 
 
