@@ -216,7 +216,7 @@ def run_ours(args, wl):
     nd = s.N_d
     nat = wl["natom"]
 
-    def context(prec, profile=1):
+    def context(prec, profile=1, tile=-1):
         c = R.Context(s.n, s.h, s.bc, s.fd_radius, stream=stream.cuda_stream)
         R.rpa_set_potential(c.ctx, s.vloc)
         R.rpa_set_projectors(c.ctx, [(g.idx, g.chi, g.gamma) for g in s.groups])
@@ -224,10 +224,11 @@ def run_ours(args, wl):
         R.rpa_set_frequencies(c.ctx, om, w)
         R.rpa_set_options(c.ctx, lanczos_max=wl["nl"], stern_tol=wl["tol"], stern_maxit=20000,
                           precision=prec, stride=wl["stride"], interp=wl["interp"],
-                          refine=args.refine, profile=profile)
+                          refine=args.refine, profile=profile, tile=tile)
         return c
 
-    cm = context("mixed")
+    mixed_form = "mixed_bf16" if args.proj == "bf16" else "mixed"
+    cm = context(mixed_form, tile=args.tile)
     P = R.rpa_num_probes(cm.ctx)
     probe_idx = torch.from_numpy(R.rpa_probe_indices(cm.ctx)).to(dev)
     dco = torch.zeros((wl["nw"], P), dtype=torch.float64, device=dev)
@@ -279,7 +280,9 @@ def run_ours(args, wl):
     ks = np.sum([st["kernel_seconds"] for st in stats], axis=0)
     kb = np.sum([st["kernel_bytes"] for st in stats], axis=0)
     kl = np.sum([st["kernel_launches"] for st in stats], axis=0)
-    names = ["proj_dots", "k_dirmatvec", "k_scalars", "k_update_dots", "none"]
+    tile_rows = int(stats[-1].get("tile_rows", 0)) if stats else 0
+    names = ["proj_dots", "k_dirmatvec_rows" if tile_rows > 0 else "k_dirmatvec", "k_scalars",
+             "k_update_dots", "none"]
     dom = 1 if ks[1] >= ks[3] else 3
     pk = peaks()
     achieved = kb[dom] / ks[dom] / 1e9 if ks[dom] > 0 else 0.0
@@ -322,10 +325,11 @@ def run_ours(args, wl):
             omx = R.rpa_probe_density(cm.ctx, pr, fqt, allow_nonconv=True)
         torch.cuda.synchronize()
         dd = (omx["d"] - o64["d"]).cpu().numpy()
-        g3 = float(np.prod(wl["stride"]))
+        g3 = nd / P
         # E_c difference estimated from the sample: per frequency the sampled mean of d_mix -
-        # d_fp64 times P (all coarse points), weighted and summed (the interpolated sum is
-        # g^3 times the coarse sum on these periodic cells), with its standard error.
+        # d_fp64 times P (all coarse points), weighted and summed, with its standard error.
+        # The interpolated fine sum weights each coarse point by N_d / P on average (exactly
+        # g^3 when g divides every periodic axis).
         est, var = 0.0, 0.0
         for k in range(wl["nw"]):
             m = fq == k
@@ -383,9 +387,16 @@ def run_ours(args, wl):
         steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * t / args.steps,
         higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32+f64",
         data="synthetic (seeded Si-like cell, synth/)",
-        config=dict(workload=wl["system"], desc=wl["desc"], form="mixed",
+        config=dict(workload=wl["system"], desc=wl["desc"], form=mixed_form,
+                    projection=("bf16 tcgen05 kind::f16, 1 pass" if args.proj == "bf16"
+                                else "tf32x3 tcgen05 kind::tf32"),
+                    stride=list(wl["stride"]), interp=wl["interp"],
                     stern_tol=wl["tol"], refine=args.refine,
                     probe_points_per_step=per * wl["nw"] * world, l2="inputs > L2 (no flush)",
+                    tile_rows=tile_rows,
+                    h_apply_tiling=(f"{tile_rows} full x rows per block" if tile_rows > 0
+                                    else "32 x 8 column tiles")
+                    + (" (autotuned)" if args.tile < 0 else " (set by --tile)"),
                     parallelism=f"probe-points sharded over {world} GPU(s)"),
         roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
         clocks=clk, fp64_form=fp64,
@@ -431,6 +442,13 @@ def main():
     ap.add_argument("--nl", type=int, default=0,
                     help="override the Lanczos step count (profiling runs only)")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--tile", type=int, default=-1,
+                    help="H-apply tiling of the mixed form: -1 autotune, 0 32x8 column tiles, "
+                         "h > 0 full-row tiles of height h")
+    ap.add_argument("--proj", default="tf32x3", choices=["tf32x3", "bf16"],
+                    help="operand form of the mixed form's projection GEMMs")
+    ap.add_argument("--stride", type=int, default=0,
+                    help="override the coarse stride g on every axis (interpolation sweep)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -439,6 +457,9 @@ def main():
     if args.nl > 0:
         wl["nl"] = args.nl
         wl["desc"] += f" [profiling run: {args.nl} Lanczos steps]"
+    if args.stride > 0:
+        wl["stride"] = (args.stride,) * 3
+        wl["desc"] += f" [stride {args.stride}]"
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
             return

@@ -55,7 +55,10 @@ enum { RPA_PERIODIC = 0, RPA_DIRICHLET = 1 };
 /* precision forms: plain FP64 everywhere, or FP32 stencil/COCG/projections with FP64
  * Lanczos basis, reorthogonalisation, tridiagonal eigen-solve, refinement residuals and
  * energy accumulation */
-enum { RPA_FP64 = 0, RPA_MIXED = 1 };
+/* RPA_FP64: every step in FP64.  RPA_MIXED: FP32 stencil/COCG with FP64 residual refinement,
+ * occupied-space projection GEMMs on the tensor cores in TF32x3 (fp32-level accuracy).
+ * RPA_MIXED_BF16: as RPA_MIXED with single-pass BF16 projection GEMMs (FP32 accumulation). */
+enum { RPA_FP64 = 0, RPA_MIXED = 1, RPA_MIXED_BF16 = 2 };
 enum { RPA_INTERP_NONE = 0, RPA_INTERP_TRILINEAR = 1, RPA_INTERP_TRICUBIC = 2,
        RPA_INTERP_FOURIER = 3 };
 /* matrix function hook (quadrature checks): f(x) = log(1-x)+x, x, or x^2 */
@@ -78,7 +81,7 @@ typedef struct {
   double lanczos_rtol;   /* early exit when |d_k - d_{k-1}| <= rtol |d_k|, k >= 2; 0 = off */
   double stern_tol;      /* Sternheimer relative residual ||b - A x||_2 <= tol ||b||_2 */
   int stern_maxit;       /* COCG iteration cap per solve (RPA_ENOCONV beyond) */
-  int precision;         /* RPA_FP64 or RPA_MIXED */
+  int precision;         /* RPA_FP64, RPA_MIXED or RPA_MIXED_BF16 */
   int reorth;            /* 1: full reorthogonalisation of the Lanczos basis (2 passes) */
   int stride[3];         /* coarsening factor g per axis (C_g of Section 3.2) */
   int interp;            /* RPA_INTERP_* */
@@ -88,6 +91,10 @@ typedef struct {
   double inner_tol;      /* mixed form: FP32 COCG relative tolerance per round
                             (0 = auto: max(sqrt(stern_tol), 1e-5)) */
   int profile;           /* 1: time the COCG kernels with CUDA events (rpa_stats.kernel_*) */
+  int tile;              /* xy tiling of the fused H-apply kernel: -1 = autotune (time the
+                            candidate tilings on the first COCG solve of each precision and
+                            keep the fastest), 0 = 32 x 8 column tiles, h > 0 = tiles of h full
+                            x rows (needs nx <= 64; RPA_EINVAL if h does not fit the grid) */
 } rpa_options;
 
 typedef struct {
@@ -109,6 +116,8 @@ typedef struct {
   long long kernel_launches[8];
   double kernel_bytes[8];
   int precision_bytes;     /* bytes of one real value in the COCG vectors (4 or 8) */
+  int tile_rows;           /* tiling the H-apply kernel used: 0 = 32 x 8 column tiles,
+                              h > 0 = full-row tiles of height h */
 } rpa_stats;
 
 /* ---- context --------------------------------------------------------------------------- */

@@ -31,7 +31,7 @@ RPA_OK, RPA_EINVAL, RPA_ENOMEM, RPA_ECUDA, RPA_ENOCONV, RPA_EBREAKDOWN, RPA_ETIM
     RPA_ENOGAP, RPA_ESTATE = range(9)
 RPA_HOST, RPA_DEVICE = 0, 1
 RPA_PERIODIC, RPA_DIRICHLET = 0, 1
-RPA_FP64, RPA_MIXED = 0, 1
+RPA_FP64, RPA_MIXED, RPA_MIXED_BF16 = 0, 1, 2
 RPA_INTERP_NONE, RPA_INTERP_TRILINEAR, RPA_INTERP_TRICUBIC, RPA_INTERP_FOURIER = range(4)
 RPA_F_LOG, RPA_F_X, RPA_F_X2 = range(3)
 INTERP = {"none": 0, "linear": 1, "trilinear": 1, "cubic": 2, "tricubic": 2, "fourier": 3}
@@ -95,7 +95,7 @@ class Options(C.Structure):
                 ("stern_maxit", C.c_int), ("precision", C.c_int), ("reorth", C.c_int),
                 ("stride", C.c_int * 3), ("interp", C.c_int), ("batch", C.c_int),
                 ("fkind", C.c_int), ("refine", C.c_int), ("inner_tol", C.c_double),
-                ("profile", C.c_int)]
+                ("profile", C.c_int), ("tile", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -105,7 +105,7 @@ class Stats(C.Structure):
                 ("refine_rounds", C.c_longlong), ("max_cocg_iters", C.c_int),
                 ("lanczos_steps_max", C.c_int), ("kernel_seconds", C.c_double * 8),
                 ("kernel_launches", C.c_longlong * 8), ("kernel_bytes", C.c_double * 8),
-                ("precision_bytes", C.c_int)]
+                ("precision_bytes", C.c_int), ("tile_rows", C.c_int)]
 
     def as_dict(self):
         return dict(seconds_total=self.seconds_total, seconds_phase=list(self.seconds_phase),
@@ -116,7 +116,7 @@ class Stats(C.Structure):
                     kernel_seconds=list(self.kernel_seconds),
                     kernel_launches=list(self.kernel_launches),
                     kernel_bytes=list(self.kernel_bytes),
-                    precision_bytes=self.precision_bytes)
+                    precision_bytes=self.precision_bytes, tile_rows=self.tile_rows)
 
 
 def _declare(lib):
@@ -285,7 +285,8 @@ def rpa_set_options(ctx, opts=None, **kw):
         elif k == "interp" and isinstance(v, str):
             o.interp = INTERP[v]
         elif k == "precision" and isinstance(v, str):
-            o.precision = {"fp64": RPA_FP64, "mixed": RPA_MIXED}[v]
+            o.precision = {"fp64": RPA_FP64, "mixed": RPA_MIXED,
+                           "mixed_bf16": RPA_MIXED_BF16}[v]
         else:
             setattr(o, k, v)
     _check(load().rpa_set_options(ctx, C.byref(o)), ctx)

@@ -95,6 +95,7 @@ struct rpa_ctx {
   cudaEvent_t pev[4 * 7];
   bool have_pev = false;
   rpa_stats* prof_stats = nullptr;
+  int tuned_ty[2] = {-1, -1};  // autotuned H-apply tiling per COCG precision (FP32, FP64)
   int prof_cpx_bytes = 0;
 };
 
@@ -299,8 +300,9 @@ static int fused_ntiles_xy(const rpa_ctx* c) {
   return ((c->grid.n[0] + 31) / 32) * ((c->grid.n[1] + 7) / 8);
 }
 static int part_stride(const rpa_ctx* c) {
-  return (int)std::max<long long>(tiles_of(c->nd),
-                                  (long long)fused_ntiles_xy(c) * fused_nzchunk(c));
+  // row tiles number at most ny per z chunk
+  const long long fused = (long long)std::max(fused_ntiles_xy(c), c->grid.n[1]) * fused_nzchunk(c);
+  return (int)std::max<long long>(tiles_of(c->nd), fused);
 }
 
 static int gram_chunks(long long nd) {
@@ -310,7 +312,7 @@ static int gram_chunks(long long nd) {
 static size_t per_probe_bytes(const rpa_ctx* c) {
   const long long nd = c->nd, ns = c->ns;
   size_t b = (size_t)ns * nd * cpx_bytes(c) * 4;
-  if (c->opt.precision == RPA_MIXED && c->opt.refine > 0) b += (size_t)ns * nd * 32;
+  if (c->opt.precision != RPA_FP64 && c->opt.refine > 0) b += (size_t)ns * nd * 32;
   b += (size_t)(c->opt.lanczos_max + 1) * nd * 8 + (size_t)nd * 8 * 5 + (size_t)nd * 4 * 3;
   b += (size_t)ns * part_stride(c) * 4 * 8 + (size_t)ns * (kSysD * 8 + kSysI * 4);
   b += (size_t)ns * ns * (gram_chunks(nd) * 8 + 16);
@@ -342,7 +344,7 @@ static rpa_status ensure_workspace(rpa_ctx* c, int nb) {
   CK(c->dens64.ensure(sizeof(double) * nb * nd));
   CK(c->t64a.ensure(sizeof(double) * nb * nd));
   CK(c->t64b.ensure(sizeof(double) * nb * nd));
-  if (c->opt.precision == RPA_MIXED) {
+  if (c->opt.precision != RPA_FP64) {
     CK(c->u32.ensure(sizeof(float) * nb * nd));
     CK(c->t32a.ensure(sizeof(float) * nb * nd));
     CK(c->t32b.ensure(sizeof(float) * nb * nd));
@@ -468,7 +470,63 @@ static FusedBufs<T> make_fused(rpa_ctx* c) {
   fb.first = 1;
   fb.nact = 0;
   fb.cd_in_smem = (sizeof(cpx<T>) * c->ngroup * kProjChunk <= 32768) ? 1 : 0;
+  fb.row_ty = 0;
   return fb;
+}
+
+template <typename T>
+static void set_tiling(const rpa_ctx* c, FusedBufs<T>& fb, int ty) {
+  fb.row_ty = ty;
+  fb.ntiles_xy = ty > 0 ? (c->grid.n[1] + ty - 1) / ty : fused_ntiles_xy(c);
+}
+
+// Tiling of the H-apply kernel.  With options.tile = -1 every candidate (the 32 x 8 column
+// tiles and each row-tile height row_candidates() lists) is timed once on the systems of the
+// first COCG loop of the precision, and the fastest is kept for the context.  Timing runs the
+// kernel in place: it reads r, p_{k-1} and the projector coefficients and writes p_k, w and
+// its partial sums, all of which the first real iteration rewrites.
+template <typename T>
+static rpa_status choose_tiling(rpa_ctx* c, const CocgView<T>& cv, FusedBufs<T>& fb) {
+  const int k = sizeof(T) == 4 ? 0 : 1;
+  int ty = c->opt.tile >= 0 ? c->opt.tile : c->tuned_ty[k];
+  if (ty < 0) {
+    int cand[17];
+    cand[0] = 0;
+    const int nc = 1 + row_candidates<T>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius,
+                                         c->ngroup, cand + 1, 16);
+    ty = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (nc > 1 && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+      FusedBufs<T> t = fb;
+      t.first = 0;  // time the steady-state form (reads p_{k-1})
+      float best = 1e30f;
+      cudaError_t err = cudaSuccess;
+      for (int i = 0; i < nc && err == cudaSuccess; ++i) {
+        set_tiling(c, t, cand[i]);
+        err = launch_dirmatvec_only<T>(cv, t, c->stream);  // warm-up
+        if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+        for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
+          err = launch_dirmatvec_only<T>(cv, t, c->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && ms < best) {
+          best = ms;
+          ty = cand[i];
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      CK(err);
+    } else if (e0) {
+      cudaEventDestroy(e0);
+    }
+    c->tuned_ty[k] = ty;
+  }
+  set_tiling(c, fb, ty);
+  if (c->prof_stats) c->prof_stats->tile_rows = ty;
+  return RPA_OK;
 }
 
 // COCG iterations until no system is active.  Expects r (and x) set for the active systems;
@@ -487,6 +545,7 @@ static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv_all, int maxit) {
   cv.list = c->list_d.as<int>();
   CKS(counts(c, cv_all.nsys, cnt, true));
   fb.nact = cnt[kActive];
+  if (fb.nact > 0) CKS(choose_tiling<T>(c, cv, fb));
   while (fb.nact > 0) {
     for (int j = 0; j < kChunkIters; ++j) {
       CK(fused_iteration<T>(cv, fb, c->opt.stern_tol, maxit, c->stream,
@@ -581,7 +640,7 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
   CK(galerkin_guess_tc(c->nd, c->ns, nb, c->d32.psi.as<float>(), c->eps_d.as<double>(),
                        c->pomega_d.as<double>(), u32, active, c->dV, c->gpart.as<double>(),
                        gram_chunks(c->nd), c->cmat.as<cpx<float>>(), x, c->flags_d.as<int>() + 2,
-                       c->stream));
+                       c->stream, c->opt.precision == RPA_MIXED_BF16));
   CK(set_status(S, c->ns, active, kActive, c->sysi.as<int>(), c->stream));
   CK(proj_dots<float>(cv.nl, c->nd, S, x, cv.sysi, 1 << kActive, cv.cdot, c->stream));
   CK((cocg_resid<float, float>(cv, x, r, p, 1 << kActive, nullptr, nullptr, nullptr, c->stream)));
@@ -654,7 +713,7 @@ static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const d
   const long long nd = c->nd;
   const int nl = c->opt.lanczos_max;
   const long long ldq = (long long)(nl + 1) * nd;
-  const bool mixed = c->opt.precision == RPA_MIXED;
+  const bool mixed = c->opt.precision != RPA_FP64;
   double* Q = c->Q.as<double>();
   int* active = c->active_d.as<int>();
   CK(cudaMemcpyAsync(c->probe_d.p, probe_h, sizeof(long long) * nb, cudaMemcpyHostToDevice,
@@ -906,6 +965,7 @@ rpa_status rpa_default_options(rpa_options* o) {
   o->fkind = RPA_F_LOG;
   o->refine = 4;
   o->inner_tol = 0.0;
+  o->tile = -1;
   return RPA_OK;
 }
 
@@ -1162,13 +1222,22 @@ rpa_status rpa_set_options(rpa_ctx* c, const rpa_options* o) {
   if (!c || !o) return RPA_EINVAL;
   if (o->lanczos_max < 1 || o->lanczos_max > kMaxLanczos) return fail(c, RPA_EINVAL, "lanczos_max out of range");
   if (!(o->stern_tol > 0.0) || o->stern_maxit < 1) return fail(c, RPA_EINVAL, "bad Sternheimer tolerance");
-  if (o->precision != RPA_FP64 && o->precision != RPA_MIXED) return fail(c, RPA_EINVAL, "bad precision");
+  if (o->precision != RPA_FP64 && o->precision != RPA_MIXED && o->precision != RPA_MIXED_BF16)
+    return fail(c, RPA_EINVAL, "bad precision");
   if (o->interp < RPA_INTERP_NONE || o->interp > RPA_INTERP_FOURIER) return fail(c, RPA_EINVAL, "bad interp");
   if (o->fkind < RPA_F_LOG || o->fkind > RPA_F_X2) return fail(c, RPA_EINVAL, "bad fkind");
   if (o->lanczos_rtol < 0.0 || o->refine < 0 || o->refine > 20 || o->batch < 0)
     return fail(c, RPA_EINVAL, "bad option");
   for (int a = 0; a < 3; ++a)
     if (o->stride[a] < 1 || o->stride[a] > c->grid.n[a]) return fail(c, RPA_EINVAL, "bad stride");
+  if (o->tile > 0) {
+    const bool ok = o->precision == RPA_FP64
+                        ? row_tile_fits<double>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, o->tile)
+                        : row_tile_fits<float>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, o->tile);
+    if (!ok) return fail(c, RPA_EINVAL, "row-tile height does not fit this grid");
+  } else if (o->tile < -1) {
+    return fail(c, RPA_EINVAL, "bad tile option");
+  }
   const bool realloc = o->precision != c->opt.precision || o->lanczos_max != c->opt.lanczos_max ||
                        o->refine != c->opt.refine;
   c->opt = *o;
@@ -1407,7 +1476,7 @@ rpa_status rpa_chi0(rpa_ctx* c, int count, const double* omega, const double* u,
                        c->stream));
     CKS(copy_in(c, c->u64.p, u + (long long)s0 * c->nd, sizeof(double) * nb * c->nd, where));
     SolveStats ss;
-    if (c->opt.precision == RPA_MIXED) {
+    if (c->opt.precision != RPA_FP64) {
       CK(convert_d2f(c->u64.as<double>(), c->u32.as<float>(), (long long)nb * c->nd, c->stream));
       CKS(solve_mixed(c, nb, c->u32.as<float>(), c->active_d.as<int>(), ss));
     } else {
@@ -1457,13 +1526,14 @@ rpa_status rpa_galerkin(rpa_ctx* c, int count, const double* omega, const double
                        c->stream));
     CKS(copy_in(c, c->u64.p, u + (long long)s0 * nd, sizeof(double) * nb * nd, where));
     const long long n = (long long)nb * c->ns * nd;
-    if (c->opt.precision == RPA_MIXED) {
+    if (c->opt.precision != RPA_FP64) {
       CK(convert_d2f(c->u64.as<double>(), c->u32.as<float>(), (long long)nb * nd, c->stream));
       CK(galerkin_guess_tc(nd, c->ns, nb, c->d32.psi.as<float>(), c->eps_d.as<double>(),
                            c->pomega_d.as<double>(), c->u32.as<float>(), c->active_d.as<int>(),
                            c->dV, c->gpart.as<double>(), gram_chunks(nd),
                            c->cmat.as<cpx<float>>(), c->x.as<cpx<float>>(),
-                           c->flags_d.as<int>() + 2, c->stream));
+                           c->flags_d.as<int>() + 2, c->stream,
+                           c->opt.precision == RPA_MIXED_BF16));
       CK(convert_f2d(c->x.as<float>(), xo.as<double>(), 2 * n, c->stream));
     } else {
       CK(galerkin_guess<double>(nd, c->ns, nb, c->d64.psi.as<double>(), c->eps_d.as<double>(),

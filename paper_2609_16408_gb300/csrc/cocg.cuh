@@ -84,7 +84,7 @@ cudaError_t galerkin_guess(long long nd, int ns, int nb, const T* psi, const dou
 cudaError_t galerkin_guess_tc(long long nd, int ns, int nb, const float* psi, const double* eps,
                               const double* omega, const float* u, const int* probe_active,
                               double dV, double* gpart, int nchunk, cpx<float>* cmat,
-                              cpx<float>* x0, int* err, cudaStream_t s);
+                              cpx<float>* x0, int* err, cudaStream_t s, bool bf16 = false);
 // Mode products along one axis of a batch of 3-D arrays: out[..a..] = sum_i Mt[i][a] in[..i..]
 // (Mt is nin x nout, row-major).  dims_in = (nx, ny, nz) of the input; batch strides in_bs and
 // out_bs.  Optional elementwise scale of the output (same layout as the output).

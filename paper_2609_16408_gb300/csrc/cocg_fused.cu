@@ -15,77 +15,11 @@
 
 #include "cocg.cuh"
 #include "cocg_fused.cuh"
+#include "fused_dev.cuh"
 
 namespace rpa {
 
-namespace {
-
-__device__ __forceinline__ int wrap_or_neg(int j, int n, int bc) {
-  if (bc == 0) {
-    while (j < 0) j += n;
-    while (j >= n) j -= n;
-    return j;
-  }
-  return (j < 0 || j >= n) ? -1 : j;
-}
-
-template <int NQ>
-__device__ __forceinline__ void block_sum(double (&v)[NQ], double* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int q = 0; q < NQ; ++q)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) sh[wid * NQ + q] = v[q];
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int w = 1; w < nw; ++w)
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) v[q] += sh[w * NQ + q];
-}
-
-// Block reduction in the working precision (the partial sums of one block are short, so
-// FP32 keeps ~1e-6 relative accuracy); thread 0 returns the totals.  FP64 arithmetic is
-// avoided here because it runs at 1/58 of the FP32 rate on this GPU.
-template <typename T, int NQ>
-__device__ __forceinline__ void block_sum_t(T (&v)[NQ], T* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int q = 0; q < NQ; ++q)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) sh[wid * NQ + q] = v[q];
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int w = 1; w < nw; ++w)
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) v[q] += sh[w * NQ + q];
-}
-
-}  // namespace
-
 constexpr int kFTX = 32, kFTY = 8;
-
-// four projector values of one entry (16-byte / 32-byte aligned vector loads)
-__device__ __forceinline__ void load_chi4(const float* p, float (&c)[4]) {
-  const float4 v = *reinterpret_cast<const float4*>(p);
-  c[0] = v.x;
-  c[1] = v.y;
-  c[2] = v.z;
-  c[3] = v.w;
-}
-__device__ __forceinline__ void load_chi4(const double* p, double (&c)[4]) {
-  const double2 a = *reinterpret_cast<const double2*>(p);
-  const double2 b = *reinterpret_cast<const double2*>(p + 2);
-  c[0] = a.x;
-  c[1] = a.y;
-  c[2] = b.x;
-  c[3] = b.y;
-}
 
 // Direction update + H apply, 2.5-D blocked (see the file comment).  All offsets inside a
 // system are 32-bit (N_d < 2^31); stencil neighbours are read from shared memory at
@@ -195,6 +129,8 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
   const int* __restrict__ p_off = cv.nl.p_off;
   const int* __restrict__ p_grp = cv.nl.p_grp;
   const T* __restrict__ p_chi = cv.nl.p_chi;
+  // next plane's potential value, projector range and first two projector entries are
+  // fetched with its stencil inputs so that their latency overlaps the current plane
   int ne0 = 0, ne1 = 0;
   auto prefetch = [&](int z) {
     const int zo = zoff(z + R);
@@ -234,7 +170,7 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
         a = caxpy_r(a, st.cy[m], cadd(cs[-m * EXN], cs[m * EXN]));
         a = caxpy_r(a, st.cz[m], cadd(zq[R - m], zq[R + m]));
       }
-      for (int e = e0; e < e1; e += 2) {  // two projector entries in flight per step
+      for (int e = e0; e < e1; e += 2) {  // the rest, two entries in flight per step
         const bool two = e + 1 < e1;
         const int g0 = p_grp[e];
         const int g1 = two ? p_grp[e + 1] : g0;
@@ -387,15 +323,18 @@ __global__ void k_proj_next(int nsys, int ngroup, const double* __restrict__ sys
 // -------------------------------------------------------------------------------------------
 template <typename T, int R>
 static void launch_dirmatvec(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s) {
-  const size_t cdb = fb.cd_in_smem ? sizeof(cpx<T>) * cv.nl.ngroup * kProjChunk : 0;
+  // the coefficients go to shared memory only while static + dynamic stay within 48 KB
+  constexpr size_t kPlanes = 2 * sizeof(cpx<T>) * (kFTX + 2 * R) * (kFTY + 2 * R);
+  size_t cdb = fb.cd_in_smem ? sizeof(cpx<T>) * cv.nl.ngroup * kProjChunk : 0;
+  if (cdb + kPlanes + 1024 > 48 * 1024) cdb = 0;
   dim3 grid(fb.ntiles_xy, fb.nact, fb.nzchunk);
   if (fb.first) {
-    if (fb.cd_in_smem)
+    if (cdb)
       k_dirmatvec<T, R, true, true><<<grid, kFTX * kFTY, cdb, s>>>(cv, fb);
     else
       k_dirmatvec<T, R, true, false><<<grid, kFTX * kFTY, 0, s>>>(cv, fb);
   } else {
-    if (fb.cd_in_smem)
+    if (cdb)
       k_dirmatvec<T, R, false, true><<<grid, kFTX * kFTY, cdb, s>>>(cv, fb);
     else
       k_dirmatvec<T, R, false, false><<<grid, kFTX * kFTY, 0, s>>>(cv, fb);
@@ -404,6 +343,11 @@ static void launch_dirmatvec(const CocgView<T>& cv, const FusedBufs<T>& fb, cuda
 
 template <typename T>
 cudaError_t launch_dirmatvec_only(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s) {
+  if (fb.row_ty > 0) {
+    cudaError_t e = launch_dirmatvec_rows<T>(cv, fb, s);
+    note_launch();
+    return e;
+  }
   switch (cv.st.R) {
     case 1: launch_dirmatvec<T, 1>(cv, fb, s); break;
     case 2: launch_dirmatvec<T, 2>(cv, fb, s); break;

@@ -16,7 +16,17 @@ struct FusedBufs {
   int ntiles_xy, nzchunk, zchunk, tiles1d, first;
   int nact;                // launched systems: the first nact entries of CocgView::list
   int cd_in_smem;          // stage the projector coefficients of a system in shared memory
+  int row_ty;              // 0: 32 x 8 column tiles; > 0: row tiles of this height (nx <= 64)
 };
+
+// whether full-row tiles of height ty can run on an nx x ny plane with stencil radius R
+template <typename T>
+bool row_tile_fits(int nx, int ny, int R, int ty);
+// row-tile heights worth timing for this grid (none when nx > 64); returns the count
+template <typename T>
+int row_candidates(int nx, int ny, int R, int ngroup, int* out, int maxn);
+template <typename T>
+cudaError_t launch_dirmatvec_rows(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s);
 
 // the direction + H-apply kernel alone (used by the tile autotuner)
 template <typename T>

@@ -1,0 +1,55 @@
+// Device helpers shared by the fused COCG kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace rpa {
+
+// periodic wrap (bc 0) of a grid index, or -1 outside a Dirichlet axis
+static __device__ __forceinline__ int wrap_or_neg(int j, int n, int bc) {
+  if (bc == 0) {
+    while (j < 0) j += n;
+    while (j >= n) j -= n;
+    return j;
+  }
+  return (j < 0 || j >= n) ? -1 : j;
+}
+
+// Block reduction in the working precision (the partial sums of one block are short, so
+// FP32 keeps ~1e-6 relative accuracy); thread 0 returns the totals.  FP64 arithmetic is
+// avoided here because it runs at 1/58 of the FP32 rate on this GPU.
+template <typename T, int NQ>
+static __device__ __forceinline__ void block_sum_t(T (&v)[NQ], T* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sh[wid * NQ + q] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < nw; ++w)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) v[q] += sh[w * NQ + q];
+}
+
+// four projector values of one entry (16-byte / 32-byte aligned vector loads)
+static __device__ __forceinline__ void load_chi4(const float* p, float (&c)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  c[0] = v.x;
+  c[1] = v.y;
+  c[2] = v.z;
+  c[3] = v.w;
+}
+static __device__ __forceinline__ void load_chi4(const double* p, double (&c)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  c[0] = a.x;
+  c[1] = a.y;
+  c[2] = b.x;
+  c[3] = b.y;
+}
+
+
+}  // namespace rpa

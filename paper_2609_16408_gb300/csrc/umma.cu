@@ -6,11 +6,18 @@
 // Operands are staged by the block's threads into shared memory in the K-major core-matrix
 // layout (8 rows x 16 bytes, no swizzle); one thread issues tcgen05.mma, accumulating in TMEM;
 // tcgen05.commit arrives on an mbarrier; the epilogue reads TMEM with tcgen05.ld.
-// Accuracy: each fp32 operand is split into tf32 hi + lo parts and the product is formed as
-// hi*hi + hi*lo + lo*hi, which keeps the result at fp32 level (a single tf32 pass would leave
-// ~5e-4 relative error in the occupied-space projection).  Every mbarrier wait is bounded;
+// Operand forms (template flag BF16):
+//   * TF32x3 (default mixed form): each fp32 operand is split into tf32 hi + lo parts and the
+//     product is formed as hi*hi + hi*lo + lo*hi, which keeps the result at fp32 level (a
+//     single tf32 pass would leave ~5e-4 relative error in the occupied-space projection).
+//   * BF16 (kind::f16, bf16 A and B, f32 accumulation): one pass on operands rounded to bf16
+//     (8-bit significand, relative rounding 2^-9).  The guess is then accurate to ~1e-2
+//     relative; COCG removes the difference, at the cost of some extra iterations.
+// Both forms use the same byte layout: a stage holds 128 bytes of K per row (32 tf32 or
+// 64 bf16).  Every mbarrier wait is bounded;
 // on expiry the kernel records an error code, waits (bounded) for its MMAs, frees TMEM and
 // returns.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "cocg.cuh"
@@ -19,8 +26,9 @@
 namespace rpa {
 
 namespace {
-constexpr int kTK = 32;                       // K elements per shared-memory stage
-constexpr uint32_t kTileBytes128 = 128 * kTK * 4;  // 128 rows x 32 tf32
+constexpr int kTK = 32;                       // tf32 K elements per shared-memory stage
+constexpr int kTK16 = 64;                     // bf16 K elements per stage (same bytes)
+constexpr uint32_t kTileBytes128 = 128 * kTK * 4;  // 128 rows x 128 bytes
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 // byte offset of (row, k) in a K-major tile of 32 tf32 per row (core matrices 8 x 16 B;
@@ -30,6 +38,26 @@ __device__ __forceinline__ uint32_t kmaj(int row, int k) {
          ((uint32_t)(k & 3) << 2);
 }
 constexpr uint32_t kLBO = 128, kSBO = 1024;
+// the same layout for 16-bit elements (8 per core-matrix row)
+__device__ __forceinline__ uint32_t kmaj16(int row, int k) {
+  return ((uint32_t)(row >> 3) << 10) + ((uint32_t)(k >> 3) << 7) + ((uint32_t)(row & 7) << 4) +
+         ((uint32_t)(k & 7) << 1);
+}
+
+__device__ __forceinline__ void put_bf16(uint8_t* t, uint32_t off, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(t + off) = __float2bfloat16_rn(v);
+}
+
+// one bf16 MMA per 16-wide K step over a 64-wide stage
+__device__ __forceinline__ void issue_stage_bf16(uint32_t tmem, uint32_t a, uint32_t b,
+                                                 uint32_t idesc, bool first) {
+#pragma unroll
+  for (int kk = 0; kk < kTK16; kk += 16) {
+    const uint32_t o = (uint32_t)kk * 16;  // 2 core matrices (16 bf16) along K
+    umma::mma_bf16(tmem, umma::smem_desc(a + o, kLBO, kSBO), umma::smem_desc(b + o, kLBO, kSBO),
+                   idesc, (first && kk == 0) ? 0u : 1u);
+  }
+}
 
 __device__ __forceinline__ void put_split(uint8_t* hi, uint8_t* lo, uint32_t off, float v) {
   const float h = umma::to_tf32(v);
@@ -55,7 +83,9 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t ahi, uint32_
 }  // namespace
 
 // gpart[b][c][k][n] = sum_{r in chunk c} psi_k(r) psi_n(r) u_b(r) for one 128 x 128 tile.
-// Dynamic shared memory: 2 stages x (A_hi, A_lo, B_hi, B_lo) x 16 KB = 128 KB.
+// Dynamic shared memory: 2 stages x (A_hi, A_lo, B_hi, B_lo) x 16 KB = 128 KB (TF32x3), or
+// 2 stages x (A, B) x 16 KB = 64 KB (BF16).
+template <bool BF16>
 __global__ void __launch_bounds__(128, 1)
     k_gram_tc(long long nd, int ns, const float* __restrict__ psi, const float* __restrict__ u,
               const int* __restrict__ active, int nchunk, long long chunk_len, int ntile_n,
@@ -85,37 +115,47 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = umma::idesc_tf32(128, nN);
+  const uint32_t idesc = BF16 ? umma::idesc_bf16(128, nN) : umma::idesc_tf32(128, nN);
   const float* ub = u + (long long)b * nd;
   const long long span = r1 > r0 ? r1 - r0 : 0;
-  const int nsteps = (int)((span + kTK - 1) / kTK);
+  constexpr int TK = BF16 ? kTK16 : kTK;
+  const int nsteps = (int)((span + TK - 1) / TK);
   bool ok = true;
   for (int step = 0; step < nsteps && ok; ++step) {
     const int st = step & 1;
     if (step >= 2) ok = umma::mbar_wait_bounded(st ? mb1 : mb0, ((step - 2) >> 1) & 1, kWaitLimit);
     if (!ok) break;
-    uint8_t* ahi = smem + st * 4 * kTileBytes128;
+    uint8_t* ahi = smem + st * (BF16 ? 2 : 4) * kTileBytes128;
     uint8_t* alo = ahi + kTileBytes128;
-    uint8_t* bhi = alo + kTileBytes128;
+    uint8_t* bhi = BF16 ? alo : alo + kTileBytes128;
     uint8_t* blo = bhi + kTileBytes128;
-    const long long rb = r0 + (long long)step * kTK;
-    for (int e = threadIdx.x; e < 128 * kTK; e += 128) {
-      const int row = e / kTK, kk = e - row * kTK;
+    const long long rb = r0 + (long long)step * TK;
+    for (int e = threadIdx.x; e < 128 * TK; e += 128) {
+      const int row = e / TK, kk = e - row * TK;
       const long long r = rb + kk;
       const bool vr = r < r1;
       const int k = k0 + row, n = n0 + row;
       const float a = (vr && k < ns) ? psi[(long long)k * nd + r] : 0.f;
       const float bv = (vr && n < ns) ? psi[(long long)n * nd + r] * ub[r] : 0.f;
-      const uint32_t off = kmaj(row, kk);
-      put_split(ahi, alo, off, a);
-      put_split(bhi, blo, off, bv);
+      if (BF16) {
+        const uint32_t off = kmaj16(row, kk);
+        put_bf16(ahi, off, a);
+        put_bf16(bhi, off, bv);
+      } else {
+        const uint32_t off = kmaj(row, kk);
+        put_split(ahi, alo, off, a);
+        put_split(bhi, blo, off, bv);
+      }
     }
     umma::fence_proxy_async();
     __syncthreads();
     if (threadIdx.x == 0) {
       umma::fence_after_sync();
-      issue_stage(tmem, umma::smem_addr(ahi), umma::smem_addr(alo), umma::smem_addr(bhi),
-                  umma::smem_addr(blo), idesc, step == 0);
+      if (BF16)
+        issue_stage_bf16(tmem, umma::smem_addr(ahi), umma::smem_addr(bhi), idesc, step == 0);
+      else
+        issue_stage(tmem, umma::smem_addr(ahi), umma::smem_addr(alo), umma::smem_addr(bhi),
+                    umma::smem_addr(blo), idesc, step == 0);
       umma::mma_commit(st ? mb1 : mb0);
     }
   }
@@ -148,8 +188,9 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // x0[(b,n)][r] = sum_k psi_k(r) C_b[k][n] for a 128-point tile and 128 states (N = 256
-// columns: re, im interleaved).  Dynamic shared memory: A_hi, A_lo (128 x 32) and B_hi, B_lo
-// (256 x 32): 96 KB, one stage.
+// columns: re, im interleaved).  Dynamic shared memory, one stage: A_hi, A_lo (128 rows) and
+// B_hi, B_lo (256 rows) of 128 bytes each, 96 KB (TF32x3); A and B only, 48 KB (BF16).
+template <bool BF16>
 __global__ void __launch_bounds__(128, 1)
     k_x0_tc(long long nd, int ns, const float* __restrict__ psi, const cpx<float>* __restrict__ cmat,
             const int* __restrict__ active, int ntile_n, int nN, cpx<float>* __restrict__ x0,
@@ -175,25 +216,29 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = umma::idesc_tf32(128, nN);
+  const uint32_t idesc = BF16 ? umma::idesc_bf16(128, nN) : umma::idesc_tf32(128, nN);
+  constexpr int TK = BF16 ? kTK16 : kTK;
   uint8_t* ahi = smem;
   uint8_t* alo = ahi + kTileBytes128;
-  uint8_t* bhi = alo + kTileBytes128;
+  uint8_t* bhi = BF16 ? alo : alo + kTileBytes128;
   uint8_t* blo = bhi + 2 * kTileBytes128;
   const cpx<float>* cb = cmat + (long long)b * ns * ns;
-  const int nsteps = (ns + kTK - 1) / kTK;
+  const int nsteps = (ns + TK - 1) / TK;
   bool ok = true;
   for (int step = 0; step < nsteps && ok; ++step) {
     if (step >= 1) ok = umma::mbar_wait_bounded(mb, (step - 1) & 1, kWaitLimit);
     if (!ok) break;
-    const int kb = step * kTK;
-    for (int e = threadIdx.x; e < 128 * kTK; e += 128) {
+    const int kb = step * TK;
+    for (int e = threadIdx.x; e < 128 * TK; e += 128) {
       const int kk = e >> 7, row = e & 127;  // consecutive threads: consecutive points
       const long long r = r0 + row;
       const float a = (r < nd && kb + kk < ns) ? psi[(long long)(kb + kk) * nd + r] : 0.f;
-      put_split(ahi, alo, kmaj(row, kk), a);
+      if (BF16)
+        put_bf16(ahi, kmaj16(row, kk), a);
+      else
+        put_split(ahi, alo, kmaj(row, kk), a);
     }
-    for (int e = threadIdx.x; e < 256 * kTK; e += 128) {
+    for (int e = threadIdx.x; e < 256 * TK; e += 128) {
       const int kk = e >> 8, j = e & 255;
       const int n = n0 + (j >> 1);
       float v = 0.f;
@@ -201,14 +246,20 @@ __global__ void __launch_bounds__(128, 1)
         const cpx<float> cv = cb[(long long)(kb + kk) * ns + n];
         v = (j & 1) ? cv.im : cv.re;
       }
-      put_split(bhi, blo, kmaj(j, kk), v);
+      if (BF16)
+        put_bf16(bhi, kmaj16(j, kk), v);
+      else
+        put_split(bhi, blo, kmaj(j, kk), v);
     }
     umma::fence_proxy_async();
     __syncthreads();
     if (threadIdx.x == 0) {
       umma::fence_after_sync();
-      issue_stage(tmem, umma::smem_addr(ahi), umma::smem_addr(alo), umma::smem_addr(bhi),
-                  umma::smem_addr(blo), idesc, step == 0);
+      if (BF16)
+        issue_stage_bf16(tmem, umma::smem_addr(ahi), umma::smem_addr(bhi), idesc, step == 0);
+      else
+        issue_stage(tmem, umma::smem_addr(ahi), umma::smem_addr(alo), umma::smem_addr(bhi),
+                    umma::smem_addr(blo), idesc, step == 0);
       umma::mma_commit(mb);
     }
   }
@@ -244,31 +295,46 @@ cudaError_t gram_coef(int ns, int nb, int nchunk, const double* gpart, const dou
                       const double* omega, const int* active, double dV, cpx<T>* cmat,
                       cudaStream_t s);
 
+template <bool BF16>
+static cudaError_t tc_attr() {
+  static bool attr = false;  // per process; the attribute is the same on every device
+  if (attr) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_gram_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (BF16 ? 4 : 8) * kTileBytes128);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_x0_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (BF16 ? 3 : 6) * kTileBytes128);
+  if (e != cudaSuccess) return e;
+  attr = true;
+  return cudaSuccess;
+}
+
 cudaError_t galerkin_guess_tc(long long nd, int ns, int nb, const float* psi, const double* eps,
                               const double* omega, const float* u, const int* probe_active,
                               double dV, double* gpart, int nchunk, cpx<float>* cmat,
-                              cpx<float>* x0, int* err, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         8 * kTileBytes128);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_x0_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             6 * kTileBytes128);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+                              cpx<float>* x0, int* err, cudaStream_t s, bool bf16) {
+  cudaError_t e = bf16 ? tc_attr<true>() : tc_attr<false>();
+  if (e != cudaSuccess) return e;
   const long long chunk_len = (nd + nchunk - 1) / nchunk;
   const int nt = (ns + 127) / 128;
   const int nN = std::min(128, ((ns + 15) / 16) * 16);
   dim3 g1(nt * nt, nb, nchunk);
-  k_gram_tc<<<g1, 128, 8 * kTileBytes128, s>>>(nd, ns, psi, u, probe_active, nchunk, chunk_len,
-                                               nt, nN, gpart, err);
-  cudaError_t e = gram_coef<float>(ns, nb, nchunk, gpart, eps, omega, probe_active, dV, cmat, s);
+  if (bf16)
+    k_gram_tc<true><<<g1, 128, 4 * kTileBytes128, s>>>(nd, ns, psi, u, probe_active, nchunk,
+                                                       chunk_len, nt, nN, gpart, err);
+  else
+    k_gram_tc<false><<<g1, 128, 8 * kTileBytes128, s>>>(nd, ns, psi, u, probe_active, nchunk,
+                                                        chunk_len, nt, nN, gpart, err);
+  e = gram_coef<float>(ns, nb, nchunk, gpart, eps, omega, probe_active, dV, cmat, s);
   if (e != cudaSuccess) return e;
   const int nN2 = std::min(256, ((2 * ns + 15) / 16) * 16);
   dim3 g3((unsigned)((nd + 127) / 128), nb * nt);
-  k_x0_tc<<<g3, 128, 6 * kTileBytes128, s>>>(nd, ns, psi, cmat, probe_active, nt, nN2, x0, err);
+  if (bf16)
+    k_x0_tc<true><<<g3, 128, 3 * kTileBytes128, s>>>(nd, ns, psi, cmat, probe_active, nt, nN2, x0,
+                                                     err);
+  else
+    k_x0_tc<false><<<g3, 128, 6 * kTileBytes128, s>>>(nd, ns, psi, cmat, probe_active, nt, nN2,
+                                                      x0, err);
   note_launch(3);
   return cudaGetLastError();
 }

@@ -107,6 +107,37 @@ def test_chi0_mixed(name):
         assert np.max(np.abs(r[i] - ref)) <= 1e-7 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("name,tile", [("per", 0), ("per", 1), ("per", 4), ("per", 11),
+                                       ("dir", 3), ("dir", 10), ("mix", 2), ("mix", 9)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_chi0_tilings(name, tile, prec):
+    """Every H-apply tiling (32 x 8 column tiles, full-row tiles of several heights, ragged
+    last tiles, halos larger than the tile) gives the oracle's chi0 u."""
+    s = sysfix(name)
+    tol = 1e-12 if prec == "fp64" else 1e-10
+    c, _, _ = ctx_for(s, precision=prec, stern_tol=tol, refine=4, stern_maxit=5000, tile=tile)
+    rng = np.random.default_rng(14)
+    u = rng.standard_normal((2, s.N_d))
+    oms = np.array([0.05, 2.5])
+    r, _ = R.rpa_chi0(c.ctx, oms, u, s.ns)
+    for i in range(2):
+        ref, _ = oracle.chi0(s, oms[i], u[i], tol=1e-12)
+        bound = 1e-8 if prec == "fp64" else 1e-7
+        assert np.max(np.abs(r[i] - ref)) <= bound * np.max(np.abs(ref))
+
+
+def test_tile_option_checked():
+    s = sysfix("per")
+    c, _, _ = ctx_for(s, precision="mixed")
+    with pytest.raises(RuntimeError):
+        R.rpa_set_options(c.ctx, precision="mixed", tile=100)  # 1000 threads > 768
+    with pytest.raises(RuntimeError):
+        R.rpa_set_options(c.ctx, precision="fp64", tile=12)  # taller than the grid
+    with pytest.raises(RuntimeError):
+        R.rpa_set_options(c.ctx, tile=-2)
+    R.rpa_set_options(c.ctx, precision="mixed", tile=11)
+
+
 def test_tridiag_and_gl():
     rng = np.random.default_rng(5)
     for k in (1, 2, 3, 7, 20, 40):
@@ -276,6 +307,74 @@ def test_galerkin_projection(name, prec):
         ref = oracle.galerkin(s, oms[i], u[i])
         tol = 1e-12 if prec == "fp64" else 5e-5
         assert np.max(np.abs(x0[i] - ref)) <= tol * np.max(np.abs(ref))
+
+
+def _bf16_x0_bound(s, omega, u):
+    """Rigorous bound on |x0_bf16 - x0| per element and component for the BF16 projection:
+    both GEMM operands are rounded to bf16 (relative 2^-9 each, products 2^-8 + 2^-18),
+    accumulated in FP32; the coefficients C' are formed in FP64 from the FP32 Gram sums and
+    rounded to bf16 again for the second GEMM."""
+    ub = 2.0 ** -9
+    up = 2 * ub + ub * ub
+    psi = s.psi
+    eps = s.eps
+    absum = np.abs(psi) @ (np.abs(psi) * np.abs(u)).T          # sum_r |psi_k||psi_n u|, k x n
+    G = psi @ (psi * u).T
+    d = eps[:, None] - eps[None, :] - 1j * omega
+    C = -s.dV * G / d
+    dC = s.dV * (up * absum + 1e-6 * absum) / np.abs(d)          # + FP32 accumulation slack
+    bre = np.abs(psi).T @ (up * np.abs(C.real) + (1 + ub) * dC)  # N_d x n
+    bim = np.abs(psi).T @ (up * np.abs(C.imag) + (1 + ub) * dC)
+    return bre.T, bim.T
+
+
+@pytest.mark.parametrize("name", ["per", "dir"])
+def test_galerkin_projection_bf16(name):
+    """Single-pass BF16 projection GEMMs (tcgen05 kind::f16) vs the oracle, element by element
+    within the rounding bound of bf16 operands."""
+    s = sysfix(name)
+    c, _, _ = ctx_for(s, precision="mixed_bf16")
+    rng = np.random.default_rng(18)
+    u = rng.standard_normal((3, s.N_d))
+    oms = np.array([0.0203, 0.69, 8.8])
+    x0 = R.rpa_galerkin(c.ctx, oms, u, s.ns)
+    for i in range(3):
+        ref = oracle.galerkin(s, oms[i], u[i])
+        bre, bim = _bf16_x0_bound(s, oms[i], u[i])
+        slack = 1e-6 * np.max(np.abs(ref))
+        assert np.all(np.abs(x0[i].real - ref.real) <= 1.01 * bre + slack)
+        assert np.all(np.abs(x0[i].imag - ref.imag) <= 1.01 * bim + slack)
+        # and it is a real approximation, not noise
+        assert np.max(np.abs(x0[i] - ref)) <= 0.05 * np.max(np.abs(ref))
+
+
+def test_galerkin_projection_bf16_si8():
+    """BF16 projection on the full Si8 cell (26^3 points: many 128-point tiles, ragged tail)."""
+    import synth
+    s = synth.named_system("si8")
+    c, _, _ = ctx_for(s, precision="mixed_bf16")
+    rng = np.random.default_rng(19)
+    u = rng.standard_normal((1, s.N_d))
+    x0 = R.rpa_galerkin(c.ctx, np.array([0.69]), u, s.ns)
+    ref = oracle.galerkin(s, 0.69, u[0])
+    bre, bim = _bf16_x0_bound(s, 0.69, u[0])
+    slack = 1e-6 * np.max(np.abs(ref))
+    assert np.all(np.abs(x0[0].real - ref.real) <= 1.01 * bre + slack)
+    assert np.all(np.abs(x0[0].imag - ref.imag) <= 1.01 * bim + slack)
+
+
+@pytest.mark.parametrize("name", ["per", "dir"])
+def test_chi0_mixed_bf16(name):
+    """The BF16 guess changes only the starting point: chi0 u still meets the solve tolerance."""
+    s = sysfix(name)
+    c, _, _ = ctx_for(s, precision="mixed_bf16", stern_tol=1e-10, refine=4, stern_maxit=5000)
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal((2, s.N_d))
+    oms = np.array([0.11, 3.2])
+    r, _ = R.rpa_chi0(c.ctx, oms, u, s.ns)
+    for i in range(2):
+        ref, _ = oracle.chi0(s, oms[i], u[i], tol=1e-12)
+        assert np.max(np.abs(r[i] - ref)) <= 1e-7 * np.max(np.abs(ref))
 
 
 def test_galerkin_projection_si8_tiles():
