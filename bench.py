@@ -224,7 +224,7 @@ def run_ours(args, wl):
         R.rpa_set_frequencies(c.ctx, om, w)
         R.rpa_set_options(c.ctx, lanczos_max=wl["nl"], stern_tol=wl["tol"], stern_maxit=20000,
                           precision=prec, stride=wl["stride"], interp=wl["interp"],
-                          refine=args.refine, profile=profile, tile=tile)
+                          refine=args.refine, profile=profile, tile=tile, graphs=args.graphs)
         return c
 
     mixed_form = "mixed_bf16" if args.proj == "bf16" else "mixed"
@@ -393,7 +393,7 @@ def run_ours(args, wl):
                     stride=list(wl["stride"]), interp=wl["interp"],
                     stern_tol=wl["tol"], refine=args.refine,
                     probe_points_per_step=per * wl["nw"] * world, l2="inputs > L2 (no flush)",
-                    tile_rows=tile_rows,
+                    tile_rows=tile_rows, cuda_graphs=bool(args.graphs),
                     h_apply_tiling=(f"{tile_rows} full x rows per block" if tile_rows > 0
                                     else "32 x 8 column tiles")
                     + (" (autotuned)" if args.tile < 0 else " (set by --tile)"),
@@ -449,6 +449,8 @@ def main():
                     help="operand form of the mixed form's projection GEMMs")
     ap.add_argument("--stride", type=int, default=0,
                     help="override the coarse stride g on every axis (interpolation sweep)")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="replay COCG chunks as captured CUDA graphs (1) or launch directly (0)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

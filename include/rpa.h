@@ -95,6 +95,8 @@ typedef struct {
                             candidate tilings on the first COCG solve of each precision and
                             keep the fastest), 0 = 32 x 8 column tiles, h > 0 = tiles of h full
                             x rows (needs nx <= 64; RPA_EINVAL if h does not fit the grid) */
+  int graphs;            /* 1: replay each chunk of fused COCG iterations as a captured CUDA
+                            graph (default); 0: launch the kernels one by one */
 } rpa_options;
 
 typedef struct {

@@ -96,6 +96,13 @@ struct rpa_ctx {
   bool have_pev = false;
   rpa_stats* prof_stats = nullptr;
   int tuned_ty[2] = {-1, -1};  // autotuned H-apply tiling per COCG precision (FP32, FP64)
+  // CUDA graphs of one chunk of fused COCG iterations, keyed by every launch parameter
+  struct ChunkGraph {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+  };
+  std::vector<ChunkGraph> graphs;
   int prof_cpx_bytes = 0;
 };
 
@@ -290,6 +297,7 @@ static size_t cpx_bytes(const rpa_ctx* c) {
 }
 
 static long long tiles_of(long long nd) { return (nd + kTile - 1) / kTile; }
+constexpr int kChunkItersMax = 4;  // COCG iterations per host check (see cocg_loop)
 
 // 2.5-D tiling of the fused H apply: 32 x 8 column tiles, z split in chunks of <= 64 planes
 static int fused_zchunk(const rpa_ctx* c) { return c->grid.n[2] <= 64 ? c->grid.n[2] : 32; }
@@ -378,7 +386,7 @@ static rpa_status ensure_workspace(rpa_ctx* c, int nb) {
   CK(c->dotpart_d.ensure(sizeof(double) * nb * 64 * (nl + 2)));
   CK(c->flags_d.ensure(sizeof(int) * 4));
   CK(c->dout_d.ensure(sizeof(double) * nb));
-  CK(c->counts_d.ensure(sizeof(int) * 16));
+  CK(c->counts_d.ensure(sizeof(int) * kNumStatus * (1 + kChunkItersMax)));
   CK(c->list_d.ensure(sizeof(int) * S));
   c->ws_nb = nb;
   return RPA_OK;
@@ -453,6 +461,9 @@ static CocgView<T> make_view(rpa_ctx* c, int nb, const T* u, cpx<T>* x, cpx<T>* 
 }
 
 constexpr int kChunkIters = 4;
+static_assert(kChunkIters <= kChunkItersMax, "counts buffer holds one slot per iteration");
+// with graphs and options.profile, one chunk in kProfEvery is launched directly with events
+constexpr int kProfEvery = 4;
 
 template <typename T>
 static FusedBufs<T> make_fused(rpa_ctx* c) {
@@ -529,6 +540,69 @@ static rpa_status choose_tiling(rpa_ctx* c, const CocgView<T>& cv, FusedBufs<T>&
   return RPA_OK;
 }
 
+// One chunk of kChunkIters fused iterations as a CUDA graph.  Launch grids cover `bucket`
+// systems (the next power of two above the active count, at most all systems); list entries
+// past the active count are -1 and those blocks return at once, so one graph per bucket
+// serves every chunk with that many or fewer active systems.  Graphs are cached on the
+// context by the bytes of every launch parameter and replayed.  They hold no events: the
+// profiling mode times directly launched sample chunks instead.
+template <typename T>
+static rpa_status run_chunk_graph(rpa_ctx* c, const CocgView<T>& cv, const FusedBufs<T>& fb,
+                                  int maxit) {
+  struct Key {
+    int tsize, maxit;
+    double tol;
+    CocgView<T> cv;
+    FusedBufs<T> fb;
+  } k;
+  std::memset(&k, 0, sizeof(k));  // padding bytes take part in the comparison
+  k.tsize = (int)sizeof(T);
+  k.maxit = maxit;
+  k.tol = c->opt.stern_tol;
+  k.cv = cv;
+  k.fb = fb;
+  const unsigned char* kb = reinterpret_cast<const unsigned char*>(&k);
+  rpa_ctx::ChunkGraph* hit = nullptr;
+  for (auto& g : c->graphs)
+    if (g.key.size() == sizeof(k) && std::memcmp(g.key.data(), kb, sizeof(k)) == 0) {
+      hit = &g;
+      break;
+    }
+  if (!hit) {
+    if (fb.row_ty > 0) CK(launch_dirmatvec_rows_prepare<T>());  // attributes before capture
+    if (c->graphs.size() >= 64) {  // bounded cache: drop the oldest
+      if (c->graphs.front().exec) cudaGraphExecDestroy(c->graphs.front().exec);
+      c->graphs.erase(c->graphs.begin());
+    }
+    const long long l0 = rpa_kernel_launches(c);
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    FusedBufs<T> f = fb;
+    cudaError_t err = cudaSuccess;
+    for (int j = 0; j < kChunkIters && err == cudaSuccess; ++j) {
+      err = fused_iteration<T>(cv, f, c->opt.stern_tol, maxit, c->stream, nullptr);
+      std::swap(f.p_in, f.p_out);
+      f.first = 0;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(c->stream, &graph);
+    const int nl = (int)(rpa_kernel_launches(c) - l0);
+    note_launch(-nl);  // captured, not launched
+    if (err == cudaSuccess) err = e_end;
+    cudaGraphExec_t exec = nullptr;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    CK(err);
+    c->graphs.emplace_back();
+    c->graphs.back().key.assign(kb, kb + sizeof(k));
+    c->graphs.back().exec = exec;
+    c->graphs.back().launches = nl;
+    hit = &c->graphs.back();
+  }
+  CK(cudaGraphLaunch(hit->exec, c->stream));
+  note_launch(hit->launches);
+  return RPA_OK;
+}
+
 // COCG iterations until no system is active.  Expects r (and x) set for the active systems;
 // forms the projector coefficients of r, then iterates the fused kernels.
 template <typename T>
@@ -546,16 +620,39 @@ static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv_all, int maxit) {
   CKS(counts(c, cv_all.nsys, cnt, true));
   fb.nact = cnt[kActive];
   if (fb.nact > 0) CKS(choose_tiling<T>(c, cv, fb));
+  const bool graphs = c->opt.graphs != 0;
+  const size_t cpxb = sizeof(cpx<T>);
+  int chunk_no = 0;
   while (fb.nact > 0) {
-    for (int j = 0; j < kChunkIters; ++j) {
-      CK(fused_iteration<T>(cv, fb, c->opt.stern_tol, maxit, c->stream,
-                            prof ? c->pev + 7 * j : nullptr));
-      std::swap(fb.p_in, fb.p_out);
-      fb.first = 0;
+    // profiled chunk: kernels launched one by one between events, with the active count
+    // recorded before each iteration for the algorithmic bytes of exactly these launches
+    const bool sample = prof && (!graphs || chunk_no % kProfEvery == 0);
+    if (graphs && !sample) {
+      FusedBufs<T> g = fb;
+      int bucket = 1;
+      while (bucket < fb.nact) bucket <<= 1;
+      g.nact = std::min(bucket, cv_all.nsys);
+      CKS(run_chunk_graph<T>(c, cv, g, maxit));
+      fb.first = 0;  // an even number of iterations leaves p_in / p_out as they were
+    } else {
+      for (int j = 0; j < kChunkIters; ++j) {
+        if (sample)
+          CK(count_status(cv_all.nsys, cv_all.sysi, c->counts_d.as<int>() + kNumStatus * (1 + j),
+                          c->stream, nullptr));
+        CK(fused_iteration<T>(cv, fb, c->opt.stern_tol, maxit, c->stream,
+                              sample ? c->pev + 7 * j : nullptr));
+        std::swap(fb.p_in, fb.p_out);
+        fb.first = 0;
+      }
     }
+    ++chunk_no;
     done_iters += kChunkIters;
+    if (sample)  // the per-iteration counts, read with the chunk-end counts below
+      CK(cudaMemcpyAsync(c->pinned + kNumStatus, c->counts_d.as<int>() + kNumStatus,
+                         sizeof(int) * kNumStatus * kChunkIters, cudaMemcpyDeviceToHost,
+                         c->stream));
     CKS(counts(c, cv_all.nsys, cnt, true));  // synchronises: the events are complete
-    if (prof) {
+    if (sample) {
       rpa_stats* st = c->prof_stats;
       for (int j = 0; j < kChunkIters; ++j) {
         // interval (i, i+1) of iteration j -> kernel class
@@ -566,22 +663,16 @@ static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv_all, int maxit) {
           st->kernel_seconds[cls[i]] += 1e-3 * ms;
           st->kernel_launches[cls[i]] += (i == 1 || i == 3) ? 1 : 0;
         }
+        const double pts = (double)c->pinned[kNumStatus * (1 + j) + kActive] * (double)c->nd;
+        st->kernel_bytes[1] += pts * 4.0 * cpxb;  // direction + H apply: read r, p; write p, w
+        st->kernel_bytes[3] += pts * 6.0 * cpxb;  // update: read x, p, r, w; write x, r
       }
+      st->precision_bytes = (int)(cpxb / 2);
     }
     fb.nact = cnt[kActive];
     if (done_iters > maxit + 2 * kChunkIters) break;  // every system is marked by then
   }
   return RPA_OK;
-}
-
-// algorithmic bytes of the COCG kernels from the per-system iteration counts
-static void account_bytes(rpa_ctx* c, long long system_iters, size_t cpxb) {
-  rpa_stats* st = c->prof_stats;
-  if (!st) return;
-  const double pts = (double)system_iters * (double)c->nd;
-  st->kernel_bytes[1] += pts * 4.0 * cpxb;  // direction + H apply: read r, p; write p, w
-  st->kernel_bytes[3] += pts * 6.0 * cpxb;  // update: read x, p, r, w; write x, r
-  st->precision_bytes = (int)(cpxb / 2);
 }
 
 // FP64 form: Galerkin guess, COCG, true-residual recheck with restart (as in the oracle).
@@ -616,7 +707,6 @@ static rpa_status solve_fp64(rpa_ctx* c, int nb, const double* u, const int* act
     if (cnt[kActive] == 0) break;
   }
   CKS(collect_stats(c, S, ss));
-  account_bytes(c, ss.iters, sizeof(cpx<double>));
   CK((density<double, double>(c->nd, c->ns, nb, c->d64.psi.as<double>(), x, active,
                               c->dens64.as<double>(), c->stream)));
   return RPA_OK;
@@ -649,7 +739,6 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
   CKS(cocg_loop<float>(c, cv, maxit));
   if (c->opt.refine <= 0) {
     CKS(collect_stats(c, S, ss));
-    account_bytes(c, ss.iters, sizeof(cpx<float>));
     CK((density<float, float>(c->nd, c->ns, nb, c->d32.psi.as<float>(), x, active,
                               c->dens64.as<double>(), c->stream)));
     return RPA_OK;
@@ -679,7 +768,6 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
     // systems corrected this round are kConverged again and are re-checked next round.
   }
   CKS(collect_stats(c, S, ss));
-  account_bytes(c, ss.iters, sizeof(cpx<float>));
   CK((density<double, double>(c->nd, c->ns, nb, c->d64.psi.as<double>(), x64, active,
                               c->dens64.as<double>(), c->stream)));
   return RPA_OK;
@@ -966,6 +1054,7 @@ rpa_status rpa_default_options(rpa_options* o) {
   o->refine = 4;
   o->inner_tol = 0.0;
   o->tile = -1;
+  o->graphs = 1;
   return RPA_OK;
 }
 
@@ -1034,6 +1123,8 @@ void rpa_destroy(rpa_ctx* c) {
     for (int i = 0; i < 8; ++i) cudaEventDestroy(c->ev[i]);
   if (c->have_pev)
     for (int i = 0; i < 4 * 7; ++i) cudaEventDestroy(c->pev[i]);
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -1238,6 +1329,7 @@ rpa_status rpa_set_options(rpa_ctx* c, const rpa_options* o) {
   } else if (o->tile < -1) {
     return fail(c, RPA_EINVAL, "bad tile option");
   }
+  if (o->graphs != 0 && o->graphs != 1) return fail(c, RPA_EINVAL, "bad graphs option");
   const bool realloc = o->precision != c->opt.precision || o->lanczos_max != c->opt.lanczos_max ||
                        o->refine != c->opt.refine;
   c->opt = *o;

@@ -249,6 +249,7 @@ __global__ void k_scalars(int nsys, int tiles, int stride, const double* __restr
   const int lane = threadIdx.x & 31;
   if (i >= nsys) return;
   const int s = list ? list[i] : i;
+  if (s < 0) return;  // past the active count of a graph launch
   int* si = sysi + (long long)s * kSysI;
   double* sd = sysd + (long long)s * kSysD;
   const int st = si[kStatus];
@@ -349,6 +350,9 @@ __global__ void k_count_status(int nsys, const int* __restrict__ sysi, int* __re
   }
   __syncthreads();
   if (threadIdx.x < kNumStatus) counts[threadIdx.x] = sc[threadIdx.x];
+  // entries past the active count are -1: launches sized above the count skip them
+  if (list)
+    for (int i = sc[kActive] + threadIdx.x; i < nsys; i += blockDim.x) list[i] = -1;
 }
 
 // set status for systems: active probes (lanczos flag) -> `on`, others -> kIdle

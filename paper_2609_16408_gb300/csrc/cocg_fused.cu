@@ -30,7 +30,7 @@ template <typename T, int R, bool FIRST, bool SMEM_CD>
 __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
     k_dirmatvec(CocgView<T> cv, FusedBufs<T> fb) {
   const int s = cv.list ? cv.list[blockIdx.y] : blockIdx.y;
-  if (cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
+  if (s < 0 || cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
   constexpr int EXN = kFTX + 2 * R, EYN = kFTY + 2 * R;
   constexpr int PLN = EXN * EYN;
   constexpr int NHALO = PLN - kFTX * kFTY;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
 template <typename T>
 __global__ void __launch_bounds__(256) k_update_dots(CocgView<T> cv, FusedBufs<T> fb) {
   const int s = cv.list ? cv.list[blockIdx.y] : blockIdx.y;
-  if (cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
+  if (s < 0 || cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
   __shared__ double sh[8 * 3];
   __shared__ cpx<T> sr[kTile];
   const long long nd = cv.nd;
@@ -309,7 +309,7 @@ __global__ void k_proj_next(int nsys, int ngroup, const double* __restrict__ sys
   const int lane = threadIdx.x & 31;
   if (i >= nsys) return;
   const int s = list ? list[i] : i;
-  if (sysi[(long long)s * kSysI + kStatus] != kActive) return;
+  if (s < 0 || sysi[(long long)s * kSysI + kStatus] != kActive) return;
   const double* sd = sysd + (long long)s * kSysD;
   const cpx<T> be = init ? mk<T>((T)0, (T)0) : mk<T>((T)sd[kBeta], (T)sd[kBeta + 1]);
   cpx<T>* p = cp + (long long)s * ngroup * kProjChunk;

@@ -27,6 +27,9 @@ template <typename T>
 int row_candidates(int nx, int ny, int R, int ngroup, int* out, int maxn);
 template <typename T>
 cudaError_t launch_dirmatvec_rows(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s);
+// one-time function attributes of the row kernels (call before a stream capture)
+template <typename T>
+cudaError_t launch_dirmatvec_rows_prepare();
 
 // the direction + H-apply kernel alone (used by the tile autotuner)
 template <typename T>

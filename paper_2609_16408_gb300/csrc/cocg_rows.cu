@@ -34,7 +34,7 @@ template <typename T, int R, bool FIRST>
 __global__ void __launch_bounds__(row_max_threads<T>())
     k_dirmatvec_rows(CocgView<T> cv, FusedBufs<T> fb, int ty, int smem_cd) {
   const int s = cv.list ? cv.list[blockIdx.y] : blockIdx.y;
-  if (cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
+  if (s < 0 || cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
   const Stencil<T>& st = cv.st;
   const int nx = st.nx, ny = st.ny, nz = st.nz;
   const int plane = nx * ny;
@@ -291,6 +291,13 @@ int row_candidates(int nx, int ny, int R, int ngroup, int* out, int maxn) {
 }
 template int row_candidates<float>(int, int, int, int, int*, int);
 template int row_candidates<double>(int, int, int, int, int*, int);
+
+template <typename T>
+cudaError_t launch_dirmatvec_rows_prepare() {
+  return rows_attr<T>();
+}
+template cudaError_t launch_dirmatvec_rows_prepare<float>();
+template cudaError_t launch_dirmatvec_rows_prepare<double>();
 
 template <typename T>
 cudaError_t launch_dirmatvec_rows(const CocgView<T>& cv, const FusedBufs<T>& fb,

@@ -338,9 +338,10 @@ def _solve_ground_state(s: System, tol=1e-10, seed=0, log=None):
         res = float(np.linalg.norm(R[:, :ns], axis=0).max())
     else:
         if any(b != PERIODIC for b in s.bc):
-            return _solve_ground_state_sparse(s, tol, seed)
-        m = ns + max(8, ns // 4)
-        th, X, res = _chfsi(s, m, tol, seed, log=log)
+            th, X, res = _solve_ground_state_sparse(s, tol, seed)
+        else:
+            m = ns + max(8, ns // 4)
+            th, X, res = _chfsi(s, m, tol, seed, log=log)
     eps = th[: ns + 1]
     psi = X[:ns] / np.sqrt(s.dV)
     # deterministic sign: largest-magnitude entry positive
@@ -544,8 +545,8 @@ def cluster_system(natom=12, box=16.0, n=40, ns=24, seed=6, fd_radius=6, **kw):
 
 
 def named_system(name: str, **kw) -> System:
-    """The workloads by name: toy (12^3), si8 (26^3), si64 (52^3), si64p (40^3), lih4 (16^3),
-    lih32 (32^3), cluster12 (40^3 Dirichlet)."""
+    """The workloads by name: toy (12^3), si8 (26^3), si16 (26x26x52), si32 (26x52x52),
+    si64 (52^3), si64p (40^3), lih4 (16^3), lih32 (32^3), cluster12 (40^3 Dirichlet)."""
     if name == "toy":
         return toy_system(**kw)
     if name == "lih4":
@@ -556,6 +557,10 @@ def named_system(name: str, **kw) -> System:
         return cluster_system(**kw)
     if name == "si8":
         return si_like_system((1, 1, 1), seed=1, **kw)
+    if name == "si16":
+        return si_like_system((1, 1, 2), seed=3, **kw)
+    if name == "si32":
+        return si_like_system((1, 2, 2), seed=4, **kw)
     if name == "si64":
         return si_like_system((2, 2, 2), seed=2, **kw)
     if name == "si64p":
