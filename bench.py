@@ -191,6 +191,7 @@ def cpu_baseline(s, wl, om, probes):
                    nthreads=cores)
     dt = time.perf_counter() - t0
     return dict(value=1.0 / (wl["nl"] * dt), unit="probe-pts/s", cores=cores, kind="oracle",
+                per_core=1.0 / (wl["nl"] * dt * cores),
                 sample=(f"1 Lanczos matrix-vector product ({s.ns} Sternheimer solves, tol "
                         f"{wl['tol']}, omega={om[k]:.4g}) of 1 probe-point; probe-pts/s = "
                         f"1/(N_l x {dt:.1f} s)"))
@@ -224,7 +225,8 @@ def run_ours(args, wl):
         R.rpa_set_frequencies(c.ctx, om, w)
         R.rpa_set_options(c.ctx, lanczos_max=wl["nl"], stern_tol=wl["tol"], stern_maxit=20000,
                           precision=prec, stride=wl["stride"], interp=wl["interp"],
-                          refine=args.refine, profile=profile, tile=tile, graphs=args.graphs)
+                          refine=args.refine, profile=profile, tile=tile, graphs=args.graphs,
+                          inner_tol=args.inner_tol)
         return c
 
     mixed_form = "mixed_bf16" if args.proj == "bf16" else "mixed"
@@ -281,8 +283,14 @@ def run_ours(args, wl):
     kb = np.sum([st["kernel_bytes"] for st in stats], axis=0)
     kl = np.sum([st["kernel_launches"] for st in stats], axis=0)
     tile_rows = int(stats[-1].get("tile_rows", 0)) if stats else 0
-    names = ["proj_dots", "k_dirmatvec_rows" if tile_rows > 0 else "k_dirmatvec", "k_scalars",
-             "k_update_dots", "none"]
+    tile_tail = int(stats[-1].get("tile_rows_tail", 0)) if stats else 0
+
+    def tiling(t):
+        return (f"{t} full x rows per block" if t > 0
+                else ("64 x 8 tiles, two x points per thread" if t == -2 else "32 x 8 column tiles"))
+    hname = ("k_dirmatvec_rows" if tile_rows > 0
+             else ("k_dirmatvec_x2" if tile_rows == -2 else "k_dirmatvec"))
+    names = ["proj_dots", hname, "k_scalars", "k_update_dots", "none"]
     dom = 1 if ks[1] >= ks[3] else 3
     pk = peaks()
     achieved = kb[dom] / ks[dom] / 1e9 if ks[dom] > 0 else 0.0
@@ -293,7 +301,7 @@ def run_ours(args, wl):
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr_path) and kl[dom] > 0:
         tj = json.load(open(tr_path)).get(names[dom])
-        if tj and tj.get("source_sha") == kernel_source_sha():
+        if tj and tj.get("source_sha") == kernel_source_sha(names[dom]):
             alg_per_sys = {1: 4, 3: 6}[dom] * 2 * stats[0]["precision_bytes"] * nd
             sys_per_launch = kb[dom] / alg_per_sys / kl[dom]
             traffic = tj["dram_bytes_per_system"] * sys_per_launch
@@ -391,19 +399,20 @@ def run_ours(args, wl):
                     projection=("bf16 tcgen05 kind::f16, 1 pass" if args.proj == "bf16"
                                 else "tf32x3 tcgen05 kind::tf32"),
                     stride=list(wl["stride"]), interp=wl["interp"],
-                    stern_tol=wl["tol"], refine=args.refine,
+                    stern_tol=wl["tol"], refine=args.refine, inner_tol=args.inner_tol or "auto",
                     probe_points_per_step=per * wl["nw"] * world, l2="inputs > L2 (no flush)",
-                    tile_rows=tile_rows, cuda_graphs=bool(args.graphs),
-                    h_apply_tiling=(f"{tile_rows} full x rows per block" if tile_rows > 0
-                                    else "32 x 8 column tiles")
-                    + (" (autotuned)" if args.tile < 0 else " (set by --tile)"),
+                    tile_rows=tile_rows, tile_rows_tail=tile_tail, cuda_graphs=bool(args.graphs),
+                    h_apply_tiling=(f"{tiling(tile_rows)} (launches over > 32 systems), "
+                                    f"{tiling(tile_tail)} (<= 32 systems)"
+                                    + (" autotuned" if args.tile == -1 else " set by --tile")),
                     parallelism=f"probe-points sharded over {world} GPU(s)"),
         roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
         clocks=clk, fp64_form=fp64,
         ec_full_seconds_est=full_pts / value,
         cocg=dict(mean_iters=tot_iters / max(1, tot_solves), solves=tot_solves,
                   max_iters=max(st["max_cocg_iters"] for st in stats) if stats else 0,
-                  refine_rounds=sum(st["refine_rounds"] for st in stats)),
+                  refine_rounds=sum(st["refine_rounds"] for st in stats),
+                  solves_per_s=world * tot_solves / t, iters_per_s=world * tot_iters / t),
         phases_s=list(np.sum([st["seconds_phase"] for st in stats], axis=0)) if stats else None,
     )
     if rank == 0:
@@ -413,62 +422,18 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
-_SRC_SHA = None
+_KERNEL_FILES = {"k_dirmatvec": "cocg_fused.cu", "k_update_dots": "cocg_fused.cu",
+                 "k_dirmatvec_x2": "cocg_x2.cu", "k_dirmatvec_rows": "cocg_rows.cu"}
 
 
-def kernel_source_sha():
-    """Hash of the CUDA sources, to tell whether stored ncu counters still apply."""
-    global _SRC_SHA
-    if _SRC_SHA is None:
-        import hashlib
-        h = hashlib.sha256()
-        csrc = os.path.join(ROOT, "paper_2609_16408_gb300", "csrc")
-        for f in sorted(os.listdir(csrc)):
-            h.update(open(os.path.join(csrc, f), "rb").read())
-        _SRC_SHA = h.hexdigest()[:16]
-    return _SRC_SHA
-
-
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="si64", choices=sorted(WORKLOADS))
-    ap.add_argument("--probes-per-freq", type=int, default=1)
-    ap.add_argument("--fp64-probes-per-freq", type=int, default=2)
-    ap.add_argument("--refine", type=int, default=4)
-    ap.add_argument("--nl", type=int, default=0,
-                    help="override the Lanczos step count (profiling runs only)")
-    ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--tile", type=int, default=-1,
-                    help="H-apply tiling of the mixed form: -1 autotune, 0 32x8 column tiles, "
-                         "h > 0 full-row tiles of height h")
-    ap.add_argument("--proj", default="tf32x3", choices=["tf32x3", "bf16"],
-                    help="operand form of the mixed form's projection GEMMs")
-    ap.add_argument("--stride", type=int, default=0,
-                    help="override the coarse stride g on every axis (interpolation sweep)")
-    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
-                    help="replay COCG chunks as captured CUDA graphs (1) or launch directly (0)")
-    ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    args = ap.parse_args()
-    wl = dict(WORKLOADS[args.workload])
-    if args.nl > 0:
-        wl["nl"] = args.nl
-        wl["desc"] += f" [profiling run: {args.nl} Lanczos steps]"
-    if args.stride > 0:
-        wl["stride"] = (args.stride,) * 3
-        wl["desc"] += f" [stride {args.stride}]"
-    if args.impl == "reference":
-        if int(os.environ.get("RANK", "0")) != 0:
-            return
-        run_reference(args, wl)
-        return
-    run_ours(args, wl)
-
-
-if __name__ == "__main__":
-    main()
+def kernel_source_sha(kernel="k_dirmatvec"):
+    """Hash of the source file that defines `kernel` plus every CUDA header, to tell whether
+    stored ncu counters still apply to the kernel being timed."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2609_16408_gb300", "csrc")
+    files = [_KERNEL_FILES.get(kernel, "cocg_fused.cu")] + sorted(
+        f for f in os.listdir(csrc) if f.endswith(".cuh"))
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]

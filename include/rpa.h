@@ -93,8 +93,9 @@ typedef struct {
   int profile;           /* 1: time the COCG kernels with CUDA events (rpa_stats.kernel_*) */
   int tile;              /* xy tiling of the fused H-apply kernel: -1 = autotune (time the
                             candidate tilings on the first COCG solve of each precision and
-                            keep the fastest), 0 = 32 x 8 column tiles, h > 0 = tiles of h full
-                            x rows (needs nx <= 64; RPA_EINVAL if h does not fit the grid) */
+                            keep the fastest), 0 = 32 x 8 column tiles, -2 = 64 x 8 tiles with
+                            two x points per thread (mixed form, even nx), h > 0 = tiles of h
+                            full x rows (needs nx <= 64); RPA_EINVAL if it does not fit */
   int graphs;            /* 1: replay each chunk of fused COCG iterations as a captured CUDA
                             graph (default); 0: launch the kernels one by one */
 } rpa_options;
@@ -118,8 +119,10 @@ typedef struct {
   long long kernel_launches[8];
   double kernel_bytes[8];
   int precision_bytes;     /* bytes of one real value in the COCG vectors (4 or 8) */
-  int tile_rows;           /* tiling the H-apply kernel used: 0 = 32 x 8 column tiles,
-                              h > 0 = full-row tiles of height h */
+  int tile_rows;           /* tiling the H-apply kernel used for launches over many systems:
+                              0 = 32 x 8 column tiles, -2 = 64 x 8 two-point tiles, h > 0 =
+                              full-row tiles of height h */
+  int tile_rows_tail;      /* the same for launches over at most 32 systems */
 } rpa_stats;
 
 /* ---- context --------------------------------------------------------------------------- */

@@ -105,7 +105,8 @@ class Stats(C.Structure):
                 ("refine_rounds", C.c_longlong), ("max_cocg_iters", C.c_int),
                 ("lanczos_steps_max", C.c_int), ("kernel_seconds", C.c_double * 8),
                 ("kernel_launches", C.c_longlong * 8), ("kernel_bytes", C.c_double * 8),
-                ("precision_bytes", C.c_int), ("tile_rows", C.c_int)]
+                ("precision_bytes", C.c_int), ("tile_rows", C.c_int),
+                ("tile_rows_tail", C.c_int)]
 
     def as_dict(self):
         return dict(seconds_total=self.seconds_total, seconds_phase=list(self.seconds_phase),
@@ -116,7 +117,8 @@ class Stats(C.Structure):
                     kernel_seconds=list(self.kernel_seconds),
                     kernel_launches=list(self.kernel_launches),
                     kernel_bytes=list(self.kernel_bytes),
-                    precision_bytes=self.precision_bytes, tile_rows=self.tile_rows)
+                    precision_bytes=self.precision_bytes, tile_rows=self.tile_rows,
+                    tile_rows_tail=self.tile_rows_tail)
 
 
 def _declare(lib):

@@ -95,7 +95,10 @@ struct rpa_ctx {
   cudaEvent_t pev[4 * 7];
   bool have_pev = false;
   rpa_stats* prof_stats = nullptr;
-  int tuned_ty[2] = {-1, -1};  // autotuned H-apply tiling per COCG precision (FP32, FP64)
+  // autotuned H-apply tiling per COCG precision (FP32, FP64) for launches over many
+  // systems (bulk) and over few (tail); -1 = not tuned yet
+  int tuned_ty[2][2] = {{-1, -1}, {-1, -1}};
+  int nsm = 0;  // multiprocessors of the device
   // CUDA graphs of one chunk of fused COCG iterations, keyed by every launch parameter
   struct ChunkGraph {
     std::vector<unsigned char> key;
@@ -307,9 +310,12 @@ static int fused_nzchunk(const rpa_ctx* c) {
 static int fused_ntiles_xy(const rpa_ctx* c) {
   return ((c->grid.n[0] + 31) / 32) * ((c->grid.n[1] + 7) / 8);
 }
+// small launches split z further (up to 8 chunks per base chunk) to fill the GPU
+constexpr int kMaxZSplit = 8;
 static int part_stride(const rpa_ctx* c) {
   // row tiles number at most ny per z chunk
-  const long long fused = (long long)std::max(fused_ntiles_xy(c), c->grid.n[1]) * fused_nzchunk(c);
+  const long long nzc = std::min<long long>(c->grid.n[2], (long long)kMaxZSplit * fused_nzchunk(c));
+  const long long fused = (long long)std::max(fused_ntiles_xy(c), c->grid.n[1]) * nzc;
   return (int)std::max<long long>(tiles_of(c->nd), fused);
 }
 
@@ -485,46 +491,74 @@ static FusedBufs<T> make_fused(rpa_ctx* c) {
   return fb;
 }
 
+// Tiling of a launch over `nact` systems: xy tiles of kind ty, and z split into chunks
+// of at least R planes until the launch has about two waves of blocks on the GPU.
 template <typename T>
-static void set_tiling(const rpa_ctx* c, FusedBufs<T>& fb, int ty) {
+static void set_tiling(const rpa_ctx* c, FusedBufs<T>& fb, int ty, int nact) {
   fb.row_ty = ty;
-  fb.ntiles_xy = ty > 0 ? (c->grid.n[1] + ty - 1) / ty : fused_ntiles_xy(c);
+  fb.ntiles_xy = ty > 0 ? (c->grid.n[1] + ty - 1) / ty
+                        : (ty == kTileX2 ? x2_tiles_xy(c->grid.n[0], c->grid.n[1])
+                                         : fused_ntiles_xy(c));
+  const int nz = c->grid.n[2], R = c->grid.fd_radius;
+  const int base = fused_zchunk(c);
+  const long long want = 6LL * std::max(1, c->nsm);
+  int zc = base;
+  for (int f = 2; f <= kMaxZSplit; f *= 2) {
+    const long long blocks = (long long)nact * fb.ntiles_xy * ((nz + zc - 1) / zc);
+    const int next = (base + f - 1) / f;
+    if (blocks >= want || next < R) break;
+    zc = next;
+  }
+  fb.zchunk = zc;
+  fb.nzchunk = (nz + zc - 1) / zc;
 }
 
-// Tiling of the H-apply kernel.  With options.tile = -1 every candidate (the 32 x 8 column
-// tiles and each row-tile height row_candidates() lists) is timed once on the systems of the
-// first COCG loop of the precision, and the fastest is kept for the context.  Timing runs the
-// kernel in place: it reads r, p_{k-1} and the projector coefficients and writes p_k, w and
-// its partial sums, all of which the first real iteration rewrites.
+constexpr int kTailSystems = 32;  // launches over at most this many systems use the tail tiling
+
+// Tiling of the H-apply kernel.  With options.tile = -1 every candidate (32 x 8 column
+// tiles, 64 x 8 two-point tiles, each row-tile height row_candidates() lists) is timed on
+// the systems of the first COCG loop of the precision — once over all of them (bulk) and
+// once over the first few (tail) — and the fastest of each is kept for the context.  Timing
+// runs the kernel in place: it reads r, p_{k-1} and the projector coefficients and writes
+// p_k, w and its partial sums, all of which the first real iteration rewrites.
 template <typename T>
-static rpa_status choose_tiling(rpa_ctx* c, const CocgView<T>& cv, FusedBufs<T>& fb) {
+static rpa_status choose_tiling(rpa_ctx* c, const CocgView<T>& cv, const FusedBufs<T>& fb,
+                                int* ty_bulk, int* ty_tail) {
   const int k = sizeof(T) == 4 ? 0 : 1;
-  int ty = c->opt.tile >= 0 ? c->opt.tile : c->tuned_ty[k];
-  if (ty < 0) {
-    int cand[17];
-    cand[0] = 0;
-    const int nc = 1 + row_candidates<T>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius,
-                                         c->ngroup, cand + 1, 16);
-    ty = 0;
+  if (c->opt.tile != -1) {
+    *ty_bulk = *ty_tail = c->opt.tile;
+    return RPA_OK;
+  }
+  if (c->tuned_ty[k][0] == -1) {
+    int cand[18];
+    int nc = 0;
+    cand[nc++] = 0;
+    if (sizeof(T) == 4 && x2_tile_fits(c->grid.n[0], c->grid.fd_radius)) cand[nc++] = kTileX2;
+    nc += row_candidates<T>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, c->ngroup, cand + nc,
+                            16);
+    int best_ty[2] = {0, 0};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (nc > 1 && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
-      FusedBufs<T> t = fb;
-      t.first = 0;  // time the steady-state form (reads p_{k-1})
-      float best = 1e30f;
       cudaError_t err = cudaSuccess;
-      for (int i = 0; i < nc && err == cudaSuccess; ++i) {
-        set_tiling(c, t, cand[i]);
-        err = launch_dirmatvec_only<T>(cv, t, c->stream);  // warm-up
-        if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
-        for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
-          err = launch_dirmatvec_only<T>(cv, t, c->stream);
-        if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
-        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-        if (err == cudaSuccess && ms < best) {
-          best = ms;
-          ty = cand[i];
+      for (int regime = 0; regime < 2; ++regime) {
+        FusedBufs<T> t = fb;
+        t.first = 0;  // time the steady-state form (reads p_{k-1})
+        t.nact = regime == 0 ? fb.nact : std::min(fb.nact, 8);
+        float best = 1e30f;
+        for (int i = 0; i < nc && err == cudaSuccess; ++i) {
+          set_tiling(c, t, cand[i], t.nact);
+          err = launch_dirmatvec_only<T>(cv, t, c->stream);  // warm-up
+          if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+          for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep)
+            err = launch_dirmatvec_only<T>(cv, t, c->stream);
+          if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+          if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+          if (err == cudaSuccess && ms < best) {
+            best = ms;
+            best_ty[regime] = cand[i];
+          }
         }
       }
       cudaEventDestroy(e0);
@@ -533,10 +567,11 @@ static rpa_status choose_tiling(rpa_ctx* c, const CocgView<T>& cv, FusedBufs<T>&
     } else if (e0) {
       cudaEventDestroy(e0);
     }
-    c->tuned_ty[k] = ty;
+    c->tuned_ty[k][0] = best_ty[0];
+    c->tuned_ty[k][1] = best_ty[1];
   }
-  set_tiling(c, fb, ty);
-  if (c->prof_stats) c->prof_stats->tile_rows = ty;
+  *ty_bulk = c->tuned_ty[k][0];
+  *ty_tail = c->tuned_ty[k][1];
   return RPA_OK;
 }
 
@@ -619,7 +654,12 @@ static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv_all, int maxit) {
   cv.list = c->list_d.as<int>();
   CKS(counts(c, cv_all.nsys, cnt, true));
   fb.nact = cnt[kActive];
-  if (fb.nact > 0) CKS(choose_tiling<T>(c, cv, fb));
+  int ty_bulk = 0, ty_tail = 0;
+  if (fb.nact > 0) CKS(choose_tiling<T>(c, cv, fb, &ty_bulk, &ty_tail));
+  if (c->prof_stats) {
+    c->prof_stats->tile_rows = ty_bulk;
+    c->prof_stats->tile_rows_tail = ty_tail;
+  }
   const bool graphs = c->opt.graphs != 0;
   const size_t cpxb = sizeof(cpx<T>);
   int chunk_no = 0;
@@ -627,24 +667,29 @@ static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv_all, int maxit) {
     // profiled chunk: kernels launched one by one between events, with the active count
     // recorded before each iteration for the algorithmic bytes of exactly these launches
     const bool sample = prof && (!graphs || chunk_no % kProfEvery == 0);
+    int width = fb.nact;  // systems a launch covers
     if (graphs && !sample) {
-      FusedBufs<T> g = fb;
       int bucket = 1;
       while (bucket < fb.nact) bucket <<= 1;
-      g.nact = std::min(bucket, cv_all.nsys);
+      width = std::min(bucket, cv_all.nsys);
+    }
+    FusedBufs<T> g = fb;
+    g.nact = width;
+    set_tiling(c, g, width <= kTailSystems ? ty_tail : ty_bulk, width);
+    if (graphs && !sample) {
       CKS(run_chunk_graph<T>(c, cv, g, maxit));
-      fb.first = 0;  // an even number of iterations leaves p_in / p_out as they were
     } else {
       for (int j = 0; j < kChunkIters; ++j) {
         if (sample)
           CK(count_status(cv_all.nsys, cv_all.sysi, c->counts_d.as<int>() + kNumStatus * (1 + j),
                           c->stream, nullptr));
-        CK(fused_iteration<T>(cv, fb, c->opt.stern_tol, maxit, c->stream,
+        CK(fused_iteration<T>(cv, g, c->opt.stern_tol, maxit, c->stream,
                               sample ? c->pev + 7 * j : nullptr));
-        std::swap(fb.p_in, fb.p_out);
-        fb.first = 0;
+        std::swap(g.p_in, g.p_out);
+        g.first = 0;
       }
     }
+    fb.first = 0;  // an even number of iterations leaves p_in / p_out as they were
     ++chunk_no;
     done_iters += kChunkIters;
     if (sample)  // the per-iteration counts, read with the chunk-end counts below
@@ -1075,7 +1120,8 @@ rpa_status rpa_create(rpa_ctx** out, const rpa_grid* g, void* stream) {
   c->nd = nd;
   c->dV = g->h[0] * g->h[1] * g->h[2];
   rpa_default_options(&c->opt);
-  if (cudaGetDevice(&c->device) != cudaSuccess) {
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
     delete c;
     return RPA_ECUDA;
   }
@@ -1321,12 +1367,15 @@ rpa_status rpa_set_options(rpa_ctx* c, const rpa_options* o) {
     return fail(c, RPA_EINVAL, "bad option");
   for (int a = 0; a < 3; ++a)
     if (o->stride[a] < 1 || o->stride[a] > c->grid.n[a]) return fail(c, RPA_EINVAL, "bad stride");
-  if (o->tile > 0) {
+  if (o->tile == kTileX2) {
+    if (o->precision == RPA_FP64 || !x2_tile_fits(c->grid.n[0], c->grid.fd_radius))
+      return fail(c, RPA_EINVAL, "two-point tiles need the mixed form and an even nx");
+  } else if (o->tile > 0) {
     const bool ok = o->precision == RPA_FP64
                         ? row_tile_fits<double>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, o->tile)
                         : row_tile_fits<float>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, o->tile);
     if (!ok) return fail(c, RPA_EINVAL, "row-tile height does not fit this grid");
-  } else if (o->tile < -1) {
+  } else if (o->tile < -2) {
     return fail(c, RPA_EINVAL, "bad tile option");
   }
   if (o->graphs != 0 && o->graphs != 1) return fail(c, RPA_EINVAL, "bad graphs option");

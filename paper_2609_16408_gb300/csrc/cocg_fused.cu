@@ -343,6 +343,15 @@ static void launch_dirmatvec(const CocgView<T>& cv, const FusedBufs<T>& fb, cuda
 
 template <typename T>
 cudaError_t launch_dirmatvec_only(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s) {
+  if (fb.row_ty == kTileX2) {
+    if constexpr (sizeof(T) == 4) {
+      cudaError_t e = launch_dirmatvec_x2(cv, fb, s);
+      note_launch();
+      return e;
+    } else {
+      return cudaErrorInvalidValue;  // FP32 only
+    }
+  }
   if (fb.row_ty > 0) {
     cudaError_t e = launch_dirmatvec_rows<T>(cv, fb, s);
     note_launch();

@@ -16,8 +16,15 @@ struct FusedBufs {
   int ntiles_xy, nzchunk, zchunk, tiles1d, first;
   int nact;                // launched systems: the first nact entries of CocgView::list
   int cd_in_smem;          // stage the projector coefficients of a system in shared memory
-  int row_ty;              // 0: 32 x 8 column tiles; > 0: row tiles of this height (nx <= 64)
+  int row_ty;              // 0: 32 x 8 column tiles; > 0: row tiles of this height (nx <= 64);
+                           // kTileX2: 64 x 8 tiles, two x points per thread (FP32, nx even)
 };
+
+constexpr int kTileX2 = -2;
+bool x2_tile_fits(int nx, int R);
+int x2_tiles_xy(int nx, int ny);
+cudaError_t launch_dirmatvec_x2(const CocgView<float>& cv, const FusedBufs<float>& fb,
+                                cudaStream_t s);
 
 // whether full-row tiles of height ty can run on an nx x ny plane with stencil radius R
 template <typename T>

@@ -108,11 +108,15 @@ def test_chi0_mixed(name):
 
 
 @pytest.mark.parametrize("name,tile", [("per", 0), ("per", 1), ("per", 4), ("per", 11),
-                                       ("dir", 3), ("dir", 10), ("mix", 2), ("mix", 9)])
+                                       ("dir", 3), ("dir", 10), ("mix", 2), ("mix", 9),
+                                       ("per", -2), ("mix", -2)])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_chi0_tilings(name, tile, prec):
-    """Every H-apply tiling (32 x 8 column tiles, full-row tiles of several heights, ragged
-    last tiles, halos larger than the tile) gives the oracle's chi0 u."""
+    """Every H-apply tiling (32 x 8 column tiles, 64 x 8 two-point tiles, full-row tiles of
+    several heights, ragged last tiles, halos larger than the tile, periodic wrap inside a
+    tile) gives the oracle's chi0 u."""
+    if tile == -2 and prec == "fp64":
+        pytest.skip("two-point tiles are an FP32 kernel")
     s = sysfix(name)
     tol = 1e-12 if prec == "fp64" else 1e-10
     c, _, _ = ctx_for(s, precision=prec, stern_tol=tol, refine=4, stern_maxit=5000, tile=tile)
@@ -134,8 +138,15 @@ def test_tile_option_checked():
     with pytest.raises(RuntimeError):
         R.rpa_set_options(c.ctx, precision="fp64", tile=12)  # taller than the grid
     with pytest.raises(RuntimeError):
-        R.rpa_set_options(c.ctx, tile=-2)
+        R.rpa_set_options(c.ctx, tile=-3)
+    with pytest.raises(RuntimeError):
+        R.rpa_set_options(c.ctx, precision="fp64", tile=-2)  # FP32 kernel only
     R.rpa_set_options(c.ctx, precision="mixed", tile=11)
+    R.rpa_set_options(c.ctx, precision="mixed", tile=-2)
+    d = sysfix("dir")  # nx = 11: pairs would straddle rows
+    cd, _, _ = ctx_for(d, precision="mixed")
+    with pytest.raises(RuntimeError):
+        R.rpa_set_options(cd.ctx, precision="mixed", tile=-2)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
