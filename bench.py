@@ -437,3 +437,56 @@ def kernel_source_sha(kernel="k_dirmatvec"):
     for f in files:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
+
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="si64", choices=sorted(WORKLOADS))
+    ap.add_argument("--probes-per-freq", type=int, default=1)
+    ap.add_argument("--fp64-probes-per-freq", type=int, default=2)
+    ap.add_argument("--refine", type=int, default=4)
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="FP32 COCG tolerance of the mixed form per refinement round (0 = auto)")
+    ap.add_argument("--nl", type=int, default=0,
+                    help="override the Lanczos step count (profiling runs only)")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--nw", type=int, default=0,
+                    help="override the frequency count (small profiling cases only)")
+    ap.add_argument("--tile", type=int, default=-1,
+                    help="H-apply tiling of the mixed form: -1 autotune, 0 32x8 column tiles, "
+                         "-2 64x8 two-point tiles, h > 0 full-row tiles of height h")
+    ap.add_argument("--proj", default="tf32x3", choices=["tf32x3", "bf16"],
+                    help="operand form of the mixed form's projection GEMMs")
+    ap.add_argument("--stride", type=int, default=0,
+                    help="override the coarse stride g on every axis (interpolation sweep)")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="replay COCG chunks as captured CUDA graphs (1) or launch directly (0)")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = dict(WORKLOADS[args.workload])
+    if args.nl > 0:
+        wl["nl"] = args.nl
+        wl["desc"] += f" [profiling run: {args.nl} Lanczos steps]"
+    if args.stride > 0:
+        wl["stride"] = (args.stride,) * 3
+        wl["desc"] += f" [stride {args.stride}]"
+    if args.nw > 0:
+        wl["nw"] = args.nw
+        wl["desc"] += f" [profiling run: {args.nw} frequencies]"
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        run_reference(args, wl)
+        return
+    run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()
