@@ -80,9 +80,9 @@ __device__ __forceinline__ void point_coords(long long p, const Stencil<T>& st, 
   ix = (int)(rem - (long long)iy * st.nx);
 }
 
-// Block reduction of NQ doubles; result valid in thread 0.
-template <int NQ>
-__device__ __forceinline__ void block_reduce(double (&v)[NQ], double* sh) {
+// Block reduction of NQ values; thread 0 returns the totals.
+template <typename A, int NQ>
+__device__ __forceinline__ void block_reduce_t(A (&v)[NQ], A* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
@@ -102,6 +102,10 @@ __device__ __forceinline__ void block_reduce(double (&v)[NQ], double* sh) {
   }
 }
 
+template <int NQ>
+__device__ __forceinline__ void block_reduce(double (&v)[NQ], double* sh) {
+  block_reduce_t<double, NQ>(v, sh);
+}
 __device__ __forceinline__ int status_of(const int* sysi, int s) {
   return sysi[(long long)s * kSysI + kStatus];
 }
@@ -119,27 +123,29 @@ __global__ void __launch_bounds__(128) k_proj_dots(NonlocalDev<T> nl, long long 
                                                    cpx<T>* __restrict__ cd) {
   const int g = blockIdx.x, s = blockIdx.y;
   if (sysi && !selected(sysi, s, mask)) return;
-  __shared__ double sh[4 * 2 * kProjChunk];
+  // sums in the working precision: a thread adds a few dozen entries, so FP32 keeps ~1e-6
+  // relative accuracy in the FP32 path without the 1/58-rate FP64 adds
+  __shared__ T sh[4 * 2 * kProjChunk];
   const cpx<T>* v = vec + (long long)s * nd;
-  double acc[2 * kProjChunk];
+  T acc[2 * kProjChunk];
 #pragma unroll
-  for (int q = 0; q < 2 * kProjChunk; ++q) acc[q] = 0.0;
+  for (int q = 0; q < 2 * kProjChunk; ++q) acc[q] = (T)0;
   for (int e = nl.g_off[g] + threadIdx.x; e < nl.g_off[g + 1]; e += blockDim.x) {
     const cpx<T> xv = v[nl.g_idx[e]];
     const T* ch = nl.g_chi + (long long)e * kProjChunk;
 #pragma unroll
     for (int l = 0; l < kProjChunk; ++l) {
-      acc[2 * l] += (double)(ch[l] * xv.re);
-      acc[2 * l + 1] += (double)(ch[l] * xv.im);
+      acc[2 * l] += ch[l] * xv.re;
+      acc[2 * l + 1] += ch[l] * xv.im;
     }
   }
-  block_reduce<2 * kProjChunk>(acc, sh);
+  block_reduce_t<T, 2 * kProjChunk>(acc, sh);
   if (threadIdx.x == 0) {
     cpx<T>* out = cd + ((long long)s * nl.ngroup + g) * kProjChunk;
 #pragma unroll
     for (int l = 0; l < kProjChunk; ++l) {
-      const double c = (double)nl.coef[g * kProjChunk + l];
-      out[l] = mk<T>((T)(c * acc[2 * l]), (T)(c * acc[2 * l + 1]));
+      const T c = nl.coef[g * kProjChunk + l];
+      out[l] = mk<T>(c * acc[2 * l], c * acc[2 * l + 1]);
     }
   }
 }

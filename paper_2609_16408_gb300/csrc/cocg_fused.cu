@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
 // this tile are one contiguous range), reduces coef * chi * r over the range with shuffles
 // and adds the tile's contribution to cr[s][g][l] with one atomic per value.
 template <typename T>
-__global__ void __launch_bounds__(256) k_update_dots(CocgView<T> cv, FusedBufs<T> fb) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_update_dots(CocgView<T> cv, FusedBufs<T> fb) {
   const int s = cv.list ? cv.list[blockIdx.y] : blockIdx.y;
   if (s < 0 || cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
   __shared__ double sh[8 * 3];
@@ -262,14 +262,28 @@ __global__ void __launch_bounds__(256) k_update_dots(CocgView<T> cv, FusedBufs<T
       T a[2 * kProjChunk];
 #pragma unroll
       for (int i = 0; i < 2 * kProjChunk; ++i) a[i] = (T)0;
-      for (int e = e0 + lane; e < e1; e += 32) {
-        const cpx<T> rv = sr[cv.nl.g_idx[e] - t0];
-        const T* ch = cv.nl.g_chi + (long long)e * kProjChunk;
+      // entries of the range, one per lane, the next one fetched while this one is used
+      int e = e0 + lane;
+      int ix = e < e1 ? cv.nl.g_idx[e] : 0;
+      T ch[kProjChunk] = {0, 0, 0, 0};
+      if (e < e1) load_chi4(cv.nl.g_chi + (long long)e * kProjChunk, ch);
+      while (e < e1) {
+        const int en = e + 32;
+        int ixn = 0;
+        T chn[kProjChunk] = {0, 0, 0, 0};
+        if (en < e1) {
+          ixn = cv.nl.g_idx[en];
+          load_chi4(cv.nl.g_chi + (long long)en * kProjChunk, chn);
+        }
+        const cpx<T> rv = sr[ix - t0];
 #pragma unroll
         for (int l = 0; l < kProjChunk; ++l) {
           a[2 * l] += ch[l] * rv.re;
           a[2 * l + 1] += ch[l] * rv.im;
+          ch[l] = chn[l];
         }
+        ix = ixn;
+        e = en;
       }
       // butterfly reduction: every lane ends with the full sums
 #pragma unroll
