@@ -171,60 +171,7 @@ __global__ void __launch_bounds__(256) k_apply_h(Stencil<T> st, const T* __restr
 }
 
 // -------------------------------------------------------------------------------------------
-// COCG kernels
-// -------------------------------------------------------------------------------------------
-// r = b - A x, b = -psi_n u_b (or b = rhs when rhs != null); optionally p = r, and for a
-// refinement round the low-precision copies r_lo = p_lo = r, x_lo = 0.
-// Partials per block: ||r||^2, ||b||^2, r^T r (re, im).
-template <typename T, typename TL>
-__global__ void __launch_bounds__(256) k_resid(CocgView<T> cv, const cpx<T>* __restrict__ x,
-                                               cpx<T>* __restrict__ r, cpx<T>* __restrict__ pdir,
-                                               int mask, cpx<TL>* __restrict__ r_lo,
-                                               cpx<TL>* __restrict__ p_lo,
-                                               cpx<TL>* __restrict__ x_lo) {
-  const int s = blockIdx.y;
-  if (!selected(cv.sysi, s, mask)) return;
-  __shared__ double sh[8 * 4];
-  const int b = s / cv.ns, n = s - b * cv.ns;
-  const long long nd = cv.nd;
-  const cpx<T> sigma = mk<T>((T)cv.eps[n], (T)cv.omega[b]);
-  const cpx<T>* xs = x + (long long)s * nd;
-  const cpx<T>* cd = cv.cdot + (long long)s * cv.nl.ngroup * kProjChunk;
-  const T* psin = cv.psi + (long long)n * nd;
-  const T* ub = cv.u + (long long)b * nd;
-  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // per-thread sums in the working precision
-  const long long t0 = (long long)blockIdx.x * kTile;
-  const long long t1 = min(t0 + kTile, nd);
-  for (long long p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
-    int ix, iy, iz;
-    point_coords(p, cv.st, ix, iy, iz);
-    const cpx<T> ax = h_at(cv.st, cv.vloc, cv.nl, xs, cd, ix, iy, iz, p, sigma);
-    const cpx<T> bv = mk<T>(-psin[p] * ub[p], (T)0);
-    const cpx<T> rv = csub(bv, ax);
-    r[(long long)s * nd + p] = rv;
-    if (pdir) pdir[(long long)s * nd + p] = rv;
-    if (r_lo) {
-      const cpx<TL> rl = mk<TL>((TL)rv.re, (TL)rv.im);
-      r_lo[(long long)s * nd + p] = rl;
-      p_lo[(long long)s * nd + p] = rl;
-      x_lo[(long long)s * nd + p] = mk<TL>((TL)0, (TL)0);
-    }
-    a0 += rv.re * rv.re + rv.im * rv.im;
-    a1 += bv.re * bv.re;
-    a2 += rv.re * rv.re - rv.im * rv.im;
-    a3 += (T)2 * rv.re * rv.im;
-  }
-  double acc[4] = {(double)a0, (double)a1, (double)a2, (double)a3};
-  block_reduce<4>(acc, sh);
-  if (threadIdx.x == 0) {
-    double* pp = cv.part + ((long long)s * cv.tiles + blockIdx.x) * 4;
-    pp[0] = acc[0];
-    pp[1] = acc[1];
-    pp[2] = acc[2];
-    pp[3] = acc[3];
-  }
-}
-
+// COCG kernels (the true residual r = b - A x is in cocg_resid.cu)
 // -------------------------------------------------------------------------------------------
 // per-system scalar steps (one warp per system, partial sums added in tile order)
 // -------------------------------------------------------------------------------------------
@@ -440,15 +387,6 @@ cudaError_t apply_h(const Stencil<T>& st, const T* vloc, const NonlocalDev<T>& n
   return cudaGetLastError();
 }
 
-template <typename T, typename TL>
-cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
-                       cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s) {
-  dim3 grid(cv.tiles, cv.nsys);
-  k_resid<T, TL><<<grid, 256, 0, s>>>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo);
-  note_launch();
-  return cudaGetLastError();
-}
-
 cudaError_t cocg_scalars(int nsys, int tiles, const double* part, double* sysd, int* sysi,
                          int kind, int mask, double tol, double inner_tol, int maxit,
                          int max_restart, cudaStream_t s, int stride, const int* list) {
@@ -511,15 +449,6 @@ template cudaError_t apply_h<double>(const Stencil<double>&, const double*,
 template cudaError_t apply_h<float>(const Stencil<float>&, const float*, const NonlocalDev<float>&,
                                     long long, int, const cpx<float>*, const cpx<float>*,
                                     cpx<float>*, cpx<float>*, cudaStream_t);
-template cudaError_t cocg_resid<double, double>(const CocgView<double>&, const cpx<double>*,
-                                                cpx<double>*, cpx<double>*, int, cpx<double>*,
-                                                cpx<double>*, cpx<double>*, cudaStream_t);
-template cudaError_t cocg_resid<double, float>(const CocgView<double>&, const cpx<double>*,
-                                               cpx<double>*, cpx<double>*, int, cpx<float>*,
-                                               cpx<float>*, cpx<float>*, cudaStream_t);
-template cudaError_t cocg_resid<float, float>(const CocgView<float>&, const cpx<float>*,
-                                              cpx<float>*, cpx<float>*, int, cpx<float>*,
-                                              cpx<float>*, cpx<float>*, cudaStream_t);
 template cudaError_t accumulate<double, float>(long long, int, const int*, int, int,
                                                const cpx<float>*, cpx<double>*, int, cudaStream_t);
 template cudaError_t density<double, double>(long long, int, int, const double*,
