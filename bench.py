@@ -304,7 +304,9 @@ def run_ours(args, wl):
         if tj and tj.get("source_sha") == kernel_source_sha(names[dom]):
             alg_per_sys = {1: 4, 3: 6}[dom] * 2 * stats[0]["precision_bytes"] * nd
             sys_per_launch = kb[dom] / alg_per_sys / kl[dom]
-            traffic = tj["dram_bytes_per_system"] * sys_per_launch
+            # per-system bytes of the captured grid, scaled to this grid's point count
+            scale = nd / tj.get("grid_points", nd)
+            traffic = tj["dram_bytes_per_system"] * scale * sys_per_launch
     roofline = dict(bound="hbm", kernel=names[dom], achieved=achieved, peak=pk["hbm_gbs"],
                     unit="GB/s", frac=achieved / pk["hbm_gbs"], traffic=traffic,
                     algorithmic_bytes_per_launch=float(kb[dom] / max(1, kl[dom])),
