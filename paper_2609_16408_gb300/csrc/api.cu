@@ -467,6 +467,8 @@ static CocgView<T> make_view(rpa_ctx* c, int nb, const T* u, cpx<T>* x, cpx<T>* 
 }
 
 constexpr int kChunkIters = 4;
+// Sternheimer tolerances at or above this use the double-float refinement residual
+constexpr double kDfResidualTol = 1e-8;
 static_assert(kChunkIters <= kChunkItersMax, "counts buffer holds one slot per iteration");
 // with graphs and options.profile, one chunk in kProfEvery is launched directly with events
 constexpr int kProfEvery = 4;
@@ -799,7 +801,9 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
   for (int round = 1; round <= c->opt.refine; ++round) {
     CK(proj_dots<double>(cv64.nl, c->nd, S, x64, cv64.sysi, 1 << kConverged, cv64.cdot,
                          c->stream));
-    CK((cocg_resid<double, float>(cv64, x64, r64, nullptr, 1 << kConverged, r, p, x, c->stream)));
+    // double-float residual while its ~2^-48 rounding stays far below the tolerance
+    CK((cocg_resid<double, float>(cv64, x64, r64, nullptr, 1 << kConverged, r, p, x, c->stream,
+                                  tol >= kDfResidualTol)));
     CK(cocg_scalars(S, cv64.tiles, cv64.part, cv64.sysd, cv64.sysi, 4, 1 << kConverged, tol, itol,
                     maxit, 0, c->stream));
     int cnt[kNumStatus];

@@ -47,7 +47,8 @@ cudaError_t apply_h(const Stencil<T>& st, const T* vloc, const NonlocalDev<T>& n
                     cudaStream_t s);
 template <typename T, typename TL>
 cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
-                       cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s);
+                       cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s,
+                       bool use_df = false);
 // Per-system scalar step (kind: 0 init, 1 alpha, 2 beta/convergence, 3 true-residual
 // recheck, 4 FP64 refinement check, 5 mixed-form init).  `tiles` partial sums per system are
 // added; `stride` (default tiles) is the per-system stride of the partial-sum buffer.

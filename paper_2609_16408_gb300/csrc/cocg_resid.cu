@@ -7,7 +7,16 @@
 // in TL = float for the next FP32 round).  Partial sums per tile: ||r||^2, ||b||^2 and
 // r^T r (re, im); partial slots beyond this launch's tiles are zeroed so that a per-system
 // sum over the full partial stride sees only this launch.
+//
+// With use_df (FP64 inputs; chosen by the caller when the solve tolerance leaves room for it)
+// the 6R-neighbour part of the stencil, which dominates the arithmetic, runs in double-float
+// arithmetic on the FP32 units (each value an unevaluated sum hi + lo of two floats; Dekker's
+// exact product through FMA and Knuth's two-sum, about 48 significant bits, i.e. ~32x the
+// FP64 rounding error) because FP64 runs at 1/58 of the FP32 rate on this GPU.  The diagonal,
+// the projector terms, b and the sums stay in FP64.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "cocg.cuh"
 #include "fused_dev.cuh"
@@ -18,11 +27,57 @@ namespace {
 
 constexpr int kRTX = 32, kRTY = 8;
 
-template <typename T, typename TL, int R, bool SMEM_CD>
+// ---- double-float arithmetic -----------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df df_of(double x) {
+  const float h = __double2float_rn(x);
+  return df{h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_val(df a) { return (double)a.hi + (double)a.lo; }
+// s + e = a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return df{s, (a - (s - bb)) + (b - bb)};
+}
+// s + e = a + b exactly, |a| >= |b|
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return df{s, b - (s - a)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+// acc + c * x with the product formed exactly in hi (Dekker's product through FMA)
+__device__ __forceinline__ df df_fma(df acc, df c, df x) {
+  const float p = c.hi * x.hi;
+  float e = fmaf(c.hi, x.hi, -p);
+  e = fmaf(c.hi, x.lo, fmaf(c.lo, x.hi, e));
+  const df s = two_sum(acc.hi, p);
+  return fast_two_sum(s.hi, s.lo + (acc.lo + e));
+}
+struct cdf {
+  df re, im;
+};
+__device__ __forceinline__ cdf cdf_of(const cpx<double>& v) { return cdf{df_of(v.re), df_of(v.im)}; }
+
+// the 6R-neighbour coefficients as double-float pairs (kernel parameters)
+struct DfCoef {
+  float hx[kMaxRadius + 1], lx[kMaxRadius + 1], hy[kMaxRadius + 1], ly[kMaxRadius + 1],
+      hz[kMaxRadius + 1], lz[kMaxRadius + 1];
+};
+
+// DF: FP64 data, 6R-neighbour sum in double-float (see the file comment)
+template <typename T, typename TL, int R, bool SMEM_CD, bool DF>
 __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
     k_resid_fused(CocgView<T> cv, const cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
                   cpx<T>* __restrict__ pdir, int mask, cpx<TL>* __restrict__ r_lo,
-                  cpx<TL>* __restrict__ p_lo, cpx<TL>* __restrict__ x_lo, int zchunk) {
+                  cpx<TL>* __restrict__ p_lo, cpx<TL>* __restrict__ x_lo, int zchunk,
+                  DfCoef dc) {
+  using V = typename std::conditional<DF, cdf, cpx<T>>::type;  // stored neighbour values
   const int s = blockIdx.y;
   const int st_s = cv.sysi[(long long)s * kSysI + kStatus];
   if (!((mask >> st_s) & 1)) return;
@@ -30,7 +85,7 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
   constexpr int PLN = EXN * EYN;
   constexpr int NHALO = PLN - kRTX * kRTY;
   constexpr int HPT = (NHALO + kRTX * kRTY - 1) / (kRTX * kRTY);
-  __shared__ cpx<T> pl[2 * PLN];
+  __shared__ V pl[2 * PLN];
   __shared__ T sh[8 * 4];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   const Stencil<T>& st = cv.st;
@@ -100,14 +155,20 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
     const int zz = wrap_or_neg(z, nz, st.bcz);
     return zz < 0 ? -1 : zz * plane;
   };
-  auto ld = [&](int q) -> cpx<T> { return q < 0 ? mk<T>((T)0, (T)0) : xs[q]; };
-  cpx<T> zq[2 * R + 1];
+  auto ld = [&](int q) -> V {
+    if constexpr (DF) {
+      return q < 0 ? cdf{df{0.f, 0.f}, df{0.f, 0.f}} : cdf_of(xs[q]);
+    } else {
+      return q < 0 ? mk<T>((T)0, (T)0) : xs[q];
+    }
+  };
+  V zq[2 * R + 1];
 #pragma unroll
   for (int i = 0; i < 2 * R; ++i) {
     const int zo = zoff(z0 - R + i);
     zq[i] = ld((zo < 0 || own_xy < 0) ? -1 : zo + own_xy);
   }
-  cpx<T> nq, hv[HPT];
+  V nq, hv[HPT];
   const bool has_nl = cv.nl.ngroup > 0;
   const int* __restrict__ p_off = cv.nl.p_off;
   const int* __restrict__ p_grp = cv.nl.p_grp;
@@ -140,16 +201,34 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
     __syncthreads();
     if (valid) {
       const int q = own_xy + z * plane;
-      const cpx<T> c = zq[R];
-      const cpx<T>* cs = pl + bo + own_slot;
+      const V* cs = pl + bo + own_slot;
       const T dg = c0 + vloc[q];
-      cpx<T> a = mk<T>(dg * c.re - (sigma.re * c.re - sigma.im * c.im),
-                       dg * c.im - (sigma.re * c.im + sigma.im * c.re));
+      cpx<T> c, a;
+      if constexpr (DF) {
+        c = mk<T>(df_val(zq[R].re), df_val(zq[R].im));
+        df sr{0.f, 0.f}, si{0.f, 0.f};
 #pragma unroll
-      for (int m = 1; m <= R; ++m) {
-        a = caxpy_r(a, st.cx[m], cadd(cs[-m], cs[m]));
-        a = caxpy_r(a, st.cy[m], cadd(cs[-m * EXN], cs[m * EXN]));
-        a = caxpy_r(a, st.cz[m], cadd(zq[R - m], zq[R + m]));
+        for (int m = 1; m <= R; ++m) {
+          const df kx{dc.hx[m], dc.lx[m]}, ky{dc.hy[m], dc.ly[m]}, kz{dc.hz[m], dc.lz[m]};
+          sr = df_fma(sr, kx, df_add(cs[-m].re, cs[m].re));
+          si = df_fma(si, kx, df_add(cs[-m].im, cs[m].im));
+          sr = df_fma(sr, ky, df_add(cs[-m * EXN].re, cs[m * EXN].re));
+          si = df_fma(si, ky, df_add(cs[-m * EXN].im, cs[m * EXN].im));
+          sr = df_fma(sr, kz, df_add(zq[R - m].re, zq[R + m].re));
+          si = df_fma(si, kz, df_add(zq[R - m].im, zq[R + m].im));
+        }
+        a = mk<T>(df_val(sr) + (dg * c.re - (sigma.re * c.re - sigma.im * c.im)),
+                  df_val(si) + (dg * c.im - (sigma.re * c.im + sigma.im * c.re)));
+      } else {
+        c = zq[R];
+        a = mk<T>(dg * c.re - (sigma.re * c.re - sigma.im * c.im),
+                  dg * c.im - (sigma.re * c.im + sigma.im * c.re));
+#pragma unroll
+        for (int m = 1; m <= R; ++m) {
+          a = caxpy_r(a, st.cx[m], cadd(cs[-m], cs[m]));
+          a = caxpy_r(a, st.cy[m], cadd(cs[-m * EXN], cs[m * EXN]));
+          a = caxpy_r(a, st.cz[m], cadd(zq[R - m], zq[R + m]));
+        }
       }
       for (int e = e0; e < e1; ++e) {
         const int g = p_grp[e];
@@ -189,7 +268,7 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
 
 template <typename T, typename TL, int R>
 void launch_r(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
-              cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s) {
+              cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, bool use_df, cudaStream_t s) {
   constexpr size_t kPlanes = 2 * sizeof(cpx<T>) * (kRTX + 2 * R) * (kRTY + 2 * R);
   size_t cdb = sizeof(cpx<T>) * cv.nl.ngroup * kProjChunk;
   if (cdb + kPlanes + 1024 > 48 * 1024) cdb = 0;
@@ -197,33 +276,57 @@ void launch_r(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, i
   const int zchunk = nz <= 64 ? nz : 32;
   const dim3 grid(((nx + kRTX - 1) / kRTX) * ((ny + kRTY - 1) / kRTY), cv.nsys,
                   (nz + zchunk - 1) / zchunk);
+  DfCoef dc{};
+  if (use_df && sizeof(T) == 8) {  // hi + lo splits of the neighbour coefficients
+    for (int m = 0; m <= R; ++m) {
+      const double v[3] = {(double)cv.st.cx[m], (double)cv.st.cy[m], (double)cv.st.cz[m]};
+      float* hi[3] = {dc.hx, dc.hy, dc.hz};
+      float* lo[3] = {dc.lx, dc.ly, dc.lz};
+      for (int a = 0; a < 3; ++a) {
+        hi[a][m] = (float)v[a];
+        lo[a][m] = (float)(v[a] - (double)hi[a][m]);
+      }
+    }
+  }
+  if constexpr (sizeof(T) == 8) {
+    if (use_df) {
+      if (cdb)
+        k_resid_fused<T, TL, R, true, true><<<grid, kRTX * kRTY, cdb, s>>>(
+            cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc);
+      else
+        k_resid_fused<T, TL, R, false, true><<<grid, kRTX * kRTY, 0, s>>>(
+            cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc);
+      return;
+    }
+  }
   if (cdb)
-    k_resid_fused<T, TL, R, true><<<grid, kRTX * kRTY, cdb, s>>>(cv, x, r, pdir, mask, r_lo,
-                                                                   p_lo, x_lo, zchunk);
+    k_resid_fused<T, TL, R, true, false><<<grid, kRTX * kRTY, cdb, s>>>(cv, x, r, pdir, mask, r_lo,
+                                                                          p_lo, x_lo, zchunk, dc);
   else
-    k_resid_fused<T, TL, R, false><<<grid, kRTX * kRTY, 0, s>>>(cv, x, r, pdir, mask, r_lo,
-                                                                  p_lo, x_lo, zchunk);
+    k_resid_fused<T, TL, R, false, false><<<grid, kRTX * kRTY, 0, s>>>(cv, x, r, pdir, mask, r_lo,
+                                                                         p_lo, x_lo, zchunk, dc);
 }
 
 }  // namespace
 
 template <typename T, typename TL>
 cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
-                       cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s) {
+                       cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s,
+                       bool use_df) {
   const int nx = cv.st.nx, ny = cv.st.ny, nz = cv.st.nz;
   const int zchunk = nz <= 64 ? nz : 32;
   const long long used = (long long)((nx + kRTX - 1) / kRTX) * ((ny + kRTY - 1) / kRTY) *
                          ((nz + zchunk - 1) / zchunk);
   if (used > cv.tiles) return cudaErrorInvalidValue;  // partial buffer too small
   switch (cv.st.R) {
-    case 1: launch_r<T, TL, 1>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, s); break;
-    case 2: launch_r<T, TL, 2>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, s); break;
-    case 3: launch_r<T, TL, 3>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, s); break;
-    case 4: launch_r<T, TL, 4>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, s); break;
-    case 5: launch_r<T, TL, 5>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, s); break;
-    case 6: launch_r<T, TL, 6>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, s); break;
-    case 7: launch_r<T, TL, 7>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, s); break;
-    default: launch_r<T, TL, 8>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, s); break;
+    case 1: launch_r<T, TL, 1>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
+    case 2: launch_r<T, TL, 2>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
+    case 3: launch_r<T, TL, 3>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
+    case 4: launch_r<T, TL, 4>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
+    case 5: launch_r<T, TL, 5>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
+    case 6: launch_r<T, TL, 6>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
+    case 7: launch_r<T, TL, 7>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
+    default: launch_r<T, TL, 8>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
   }
   note_launch();
   return cudaGetLastError();
@@ -231,12 +334,12 @@ cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>
 
 template cudaError_t cocg_resid<double, double>(const CocgView<double>&, const cpx<double>*,
                                                 cpx<double>*, cpx<double>*, int, cpx<double>*,
-                                                cpx<double>*, cpx<double>*, cudaStream_t);
+                                                cpx<double>*, cpx<double>*, cudaStream_t, bool);
 template cudaError_t cocg_resid<double, float>(const CocgView<double>&, const cpx<double>*,
                                                cpx<double>*, cpx<double>*, int, cpx<float>*,
-                                               cpx<float>*, cpx<float>*, cudaStream_t);
+                                               cpx<float>*, cpx<float>*, cudaStream_t, bool);
 template cudaError_t cocg_resid<float, float>(const CocgView<float>&, const cpx<float>*,
                                               cpx<float>*, cpx<float>*, int, cpx<float>*,
-                                              cpx<float>*, cpx<float>*, cudaStream_t);
+                                              cpx<float>*, cpx<float>*, cudaStream_t, bool);
 
 }  // namespace rpa

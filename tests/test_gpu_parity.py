@@ -171,6 +171,22 @@ def test_graph_replay_matches_direct_launches(prec):
     assert st["kernel_seconds"][1] > 0 and st["kernel_launches"][1] > 0
 
 
+@pytest.mark.parametrize("name", ["per", "dir"])
+def test_chi0_mixed_double_float_residual(name):
+    """At Sternheimer tolerances >= 1e-8 the FP64 refinement residual runs its neighbour sum in
+    double-float arithmetic (~48-bit); chi0 u still agrees with the oracle to the accuracy
+    the tolerance allows (|dr| <= cond * tol with cond < 100 at these frequencies)."""
+    s = sysfix(name)
+    c, _, _ = ctx_for(s, precision="mixed", stern_tol=1e-7, refine=6, stern_maxit=5000)
+    rng = np.random.default_rng(24)
+    u = rng.standard_normal((2, s.N_d))
+    oms = np.array([0.11, 3.2])
+    r, _ = R.rpa_chi0(c.ctx, oms, u, s.ns)
+    for i in range(2):
+        ref, _ = oracle.chi0(s, oms[i], u[i], tol=1e-12)
+        assert np.max(np.abs(r[i] - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
 def test_tridiag_and_gl():
     rng = np.random.default_rng(5)
     for k in (1, 2, 3, 7, 20, 40):
