@@ -243,6 +243,80 @@ def lanczos(s, probes, omegas, nl, tol=1e-10, maxit=5000, lrtol=0.0, reorth=1, f
     return dict(d=d, steps=steps, alpha=al, beta=be, cocg_iters=ci)
 
 
+def _fval(x, fkind):
+    if fkind == F_X:
+        return x
+    if fkind == F_X2:
+        return x * x
+    return np.log1p(-x) + x
+
+
+def block_lanczos(s, probes, omega, nl, tol=1e-10, maxit=5000, fkind=F_LOG, nthreads=0):
+    """Block Lanczos quadrature for one frequency: the b probes share one block Krylov
+    recurrence started from Q_1 = [e_j1 ... e_jb] (the block variant of the Lanczos
+    quadrature of Section 3.1 that Section 6 names as future work).  After k block steps,
+    d_ji = [E_1^T f(T_k) E_1]_ii with the block tridiagonal T_k (diagonal blocks
+    A_m = Q_m^T A Q_m, sub-diagonal blocks B_m from the QR factorisation of the next block):
+    a block Gauss rule, exact for f of degree <= 2k - 1.  As in the scalar oracle the new
+    block is reorthogonalised against every previous block by two classical Gram-Schmidt
+    passes; its QR factorisation is Cholesky QR applied twice.  Stops early (fewer steps) when
+    a pivot of the factorisation falls below 1e-14 |A_1|.  Returns dict(d, steps)."""
+    probes = np.ascontiguousarray(probes, dtype=np.int64)
+    b = len(probes)
+    N = s.N_d
+    Q = np.zeros((N, b))
+    Q[probes, np.arange(b)] = 1.0
+    blocks = [Q]
+    A_blk, B_blk = [], []
+    steps = 0
+    scale = None
+    for k in range(nl):
+        U = nu_half(s, Q.T)                                            # b x N
+        Rr = np.stack([chi0(s, omega, U[i], tol=tol, maxit=maxit, nthreads=nthreads)[0]
+                       for i in range(b)])
+        V = nu_half(s, Rr).T                                           # N x b
+        Ak = Q.T @ V
+        A_blk.append(0.5 * (Ak + Ak.T))
+        if scale is None:
+            scale = np.max(np.abs(A_blk[0]))
+        steps = k + 1
+        if k == nl - 1:
+            break
+        Qall = np.hstack(blocks)
+        for _ in range(2):
+            V = V - Qall @ (Qall.T @ V)
+        # Cholesky QR, twice: V = Q_{k+1} R2 R1
+        Rs = []
+        ok = True
+        for _ in range(2):
+            G = V.T @ V
+            try:
+                L = np.linalg.cholesky(0.5 * (G + G.T))
+            except np.linalg.LinAlgError:
+                ok = False
+                break
+            Rm = L.T
+            if np.min(np.abs(np.diag(Rm))) <= 1e-14 * scale:
+                ok = False
+                break
+            V = np.linalg.solve(Rm.T, V.T).T                           # V R^-1
+            Rs.append(Rm)
+        if not ok:
+            break
+        B_blk.append(Rs[1] @ Rs[0])
+        Q = V
+        blocks.append(Q)
+    T = np.zeros((steps * b, steps * b))
+    for k in range(steps):
+        T[k * b:(k + 1) * b, k * b:(k + 1) * b] = A_blk[k]
+        if k + 1 < steps:
+            T[(k + 1) * b:(k + 2) * b, k * b:(k + 1) * b] = B_blk[k]
+            T[k * b:(k + 1) * b, (k + 1) * b:(k + 2) * b] = B_blk[k].T
+    lam, W = np.linalg.eigh(T)
+    d = (W[:b, :] ** 2) @ _fval(lam, fkind)
+    return dict(d=d, steps=steps)
+
+
 # ---------------------------------------------------------------------------------------
 # coarse grid C_g and interpolation I_g (Section 3.2)
 # ---------------------------------------------------------------------------------------

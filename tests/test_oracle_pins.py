@@ -203,6 +203,35 @@ def test_lanczos_converges_to_exact_diagonal(tiny_exact):
     assert np.max(np.abs(d - dex[probes])) < 1e-9 * np.max(np.abs(dex))
 
 
+def test_block_lanczos_single_probe_equals_scalar(tiny_exact):
+    """A block of one probe is the scalar recurrence (independent code: C scalar Lanczos)."""
+    s, omega, out = tiny_exact
+    for j in (3, 150, s.N_d - 2):
+        a = oracle.block_lanczos(s, [j], omega, 5, tol=1e-13)["d"]
+        b = oracle.lanczos(s, np.array([j]), omega, 5, tol=1e-13)["d"]
+        assert np.allclose(a, b, rtol=1e-10, atol=1e-16)
+
+
+def test_block_gauss_exactness(tiny_exact):
+    """The block Gauss rule after k block steps is exact for degree <= 2k - 1: one step
+    gives A_jj for f = x, two steps give (A^2)_jj for f = x^2, for every probe of the block."""
+    s, omega, out = tiny_exact
+    A = out[0][3]
+    probes = np.array([0, 17, 100, s.N_d - 1])
+    r1 = oracle.block_lanczos(s, probes, omega, 1, tol=1e-13, fkind=oracle.F_X)
+    assert np.allclose(r1["d"], np.diag(A)[probes], rtol=1e-9, atol=1e-16)
+    r2 = oracle.block_lanczos(s, probes, omega, 2, tol=1e-13, fkind=oracle.F_X2)
+    assert np.allclose(r2["d"], np.sum(A[:, probes] ** 2, axis=0), rtol=1e-9, atol=1e-16)
+
+
+def test_block_lanczos_converges_to_exact_diagonal(tiny_exact):
+    s, omega, out = tiny_exact
+    dex = out[0][0]
+    probes = np.array([5, 60, 200, 301])
+    d = oracle.block_lanczos(s, probes, omega, 8, tol=1e-13)["d"]
+    assert np.max(np.abs(d - dex[probes])) < 1e-9 * np.max(np.abs(dex))
+
+
 def test_tridiag_f11_against_library_eigensolver():
     import scipy.linalg as sla
     rng = np.random.default_rng(5)
