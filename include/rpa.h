@@ -98,6 +98,11 @@ typedef struct {
                             full x rows (needs nx <= 64); RPA_EINVAL if it does not fit */
   int graphs;            /* 1: replay each chunk of fused COCG iterations as a captured CUDA
                             graph (default); 0: launch the kernels one by one */
+  int lanczos_block;     /* 1: scalar Lanczos quadrature per probe (Section 3.1, default);
+                            b in 2..8: block Lanczos quadrature, up to b consecutive probe-points
+                            of one frequency and distinct grid points share one block
+                            recurrence (the block variant named as future work in Section 6);
+                            needs reorth = 1 and lanczos_rtol = 0; no tridiagonal output */
 } rpa_options;
 
 typedef struct {

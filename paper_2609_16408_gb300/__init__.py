@@ -95,7 +95,8 @@ class Options(C.Structure):
                 ("stern_maxit", C.c_int), ("precision", C.c_int), ("reorth", C.c_int),
                 ("stride", C.c_int * 3), ("interp", C.c_int), ("batch", C.c_int),
                 ("fkind", C.c_int), ("refine", C.c_int), ("inner_tol", C.c_double),
-                ("profile", C.c_int), ("tile", C.c_int), ("graphs", C.c_int)]
+                ("profile", C.c_int), ("tile", C.c_int), ("graphs", C.c_int),
+                ("lanczos_block", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -84,6 +84,8 @@ struct rpa_ctx {
   // wave workspace
   DevBuf Q, u64, v64, dens64, t64a, t64b, u32, t32a, t32b;
   DevBuf x, r, p, p2, w, x64, r64, cdot, cpb, crb, part, sysd, sysi, gpart, cmat;
+  // block Lanczos (options.lanczos_block > 1)
+  DevBuf bD, bpart, bA, bB, bR, bRinv, bT, bW, blam, bsteps, bm, bfirst, bsize, bstart, bsz;
   DevBuf probe_d, pomega_d, active_d, steps_d, alpha_d, beta_d, lstate_d, coef_d, dots_d,
       dotpart_d, flags_d, dout_d, counts_d, list_d;
   int ws_nb = 0;
@@ -845,8 +847,15 @@ static rpa_status timing_add(rpa_ctx* c, rpa_stats* st, int from, int to, int ph
   return RPA_OK;
 }
 
+// Block layout of a wave for block Lanczos: slot s belongs to the block of consecutive slots
+// starting at first[s] with size[s] members (all one frequency, distinct points).
+struct BlockLayout {
+  std::vector<int> first, size;  // per slot
+  std::vector<int> start, sz;    // per block
+};
+
 static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const double* omega_h,
-                           WaveOut out, rpa_stats* st) {
+                           WaveOut out, rpa_stats* st, const BlockLayout* blk = nullptr) {
   const long long nd = c->nd;
   const int nl = c->opt.lanczos_max;
   const long long ldq = (long long)(nl + 1) * nd;
@@ -873,6 +882,44 @@ static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const d
   double* dpart = c->dotpart_d.as<double>();
   double* coef = c->coef_d.as<double>();
   double* v = c->v64.as<double>();
+  const int bmax = c->opt.lanczos_block;
+  const int nblk = blk ? (int)blk->start.size() : 0;
+  int *bfirst = nullptr, *bsize = nullptr, *bstart = nullptr, *bsz = nullptr, *bsteps = nullptr;
+  const long long ldT = (long long)nl * bmax * nl * bmax, ldl = (long long)nl * bmax;
+  if (blk) {
+    const size_t ntj = (size_t)bmax * (nl + 1);
+    CK(c->bD.ensure(sizeof(double) * nb * ntj));
+    CK(c->bpart.ensure(sizeof(double) * nb * ntj * nchunk));
+    CK(c->bA.ensure(sizeof(double) * nblk * nl * 64));
+    CK(c->bB.ensure(sizeof(double) * nblk * nl * 64));
+    CK(c->bR.ensure(sizeof(double) * nblk * 64));
+    CK(c->bRinv.ensure(sizeof(double) * nblk * 64));
+    CK(c->bT.ensure(sizeof(double) * nblk * ldT));
+    CK(c->bW.ensure(sizeof(double) * nblk * ldT));
+    CK(c->blam.ensure(sizeof(double) * nblk * ldl));
+    CK(c->bsteps.ensure(sizeof(int) * nblk));
+    CK(c->bm.ensure(sizeof(int) * nblk));
+    CK(c->bfirst.ensure(sizeof(int) * nb));
+    CK(c->bsize.ensure(sizeof(int) * nb));
+    CK(c->bstart.ensure(sizeof(int) * nblk));
+    CK(c->bsz.ensure(sizeof(int) * nblk));
+    bfirst = c->bfirst.as<int>();
+    bsize = c->bsize.as<int>();
+    bstart = c->bstart.as<int>();
+    bsz = c->bsz.as<int>();
+    bsteps = c->bsteps.as<int>();
+    CK(cudaMemcpyAsync(bfirst, blk->first.data(), sizeof(int) * nb, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(bsize, blk->size.data(), sizeof(int) * nb, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(bstart, blk->start.data(), sizeof(int) * nblk, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(bsz, blk->sz.data(), sizeof(int) * nblk, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemsetAsync(bsteps, 0, sizeof(int) * nblk, c->stream));
+    CK(cudaStreamSynchronize(c->stream));  // the host vectors may go away
+  }
+  int steps_done = 0;
   for (int k = 0; k < nl; ++k) {
     SolveStats ss;
     CKS(timing_mark(c, 0));
@@ -900,25 +947,53 @@ static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const d
                                            c->t64a.as<double>(), c->t64b.as<double>())));
     }
     CKS(timing_mark(c, 3));
-    // alpha_k = q_k^T v ; v -= alpha_k q_k + beta_{k-1} q_{k-1}
-    CK(multi_dot(nd, nb, Q, ldq, k, k + 1, v, active, dpart, nchunk, dots, c->stream));
-    CK(lanczos_alpha(nb, k, nl, dots, active, c->alpha_d.as<double>(), c->beta_d.as<double>(),
-                     coef, c->stream));
-    CK(multi_axpy(nd, nb, Q, ldq, std::max(0, k - 1), k + 1, k > 0 ? coef : coef + 1, 2, v,
-                  active, c->stream));
-    if (c->opt.reorth) {
+    if (blk) {
+      // block step: projections on every previous block (two classical Gram-Schmidt passes,
+      // the first also giving the diagonal block A_k), then Cholesky QR twice -> Q_{k+1}, B_k
+      const int nj = k + 1, ldD = bmax * nj;
+      double* D = c->bD.as<double>();
       for (int pass = 0; pass < 2; ++pass) {
-        CK(multi_dot(nd, nb, Q, ldq, 0, k + 1, v, active, dpart, nchunk, dots, c->stream));
-        CK(multi_axpy(nd, nb, Q, ldq, 0, k + 1, dots, k + 1, v, active, c->stream));
+        CK(block_dot(nd, nb, bmax, bfirst, bsize, Q, ldq, nd, 0, nj, v, active,
+                     c->bpart.as<double>(), nchunk, D, c->stream));
+        if (pass == 0)
+          CK(block_store_a(nblk, bstart, bsz, D, ldD, nj, k, nl, c->bA.as<double>(), active,
+                           c->stream));
+        CK(block_axpy(nd, nb, bfirst, bsize, Q, ldq, nj, D, ldD, v, active, c->stream));
       }
+      if (k + 1 < nl) {
+        for (int pass = 0; pass < 2; ++pass) {
+          CK(block_dot(nd, nb, bmax, bfirst, bsize, v, nd, nd, 0, 1, v, active,
+                       c->bpart.as<double>(), nchunk, D, c->stream));
+          CK(block_chol(nblk, bstart, bsz, D, bmax, pass, k, nl, c->bA.as<double>(),
+                        c->bR.as<double>(), c->bRinv.as<double>(), c->bB.as<double>(), active,
+                        bsteps, c->stream));
+          CK(block_scale(nd, nblk, bstart, bsz, c->bRinv.as<double>(), v,
+                         pass == 0 ? v : Q + (long long)(k + 1) * nd, pass == 0 ? nd : ldq,
+                         active, c->stream));
+        }
+      }
+      steps_done = k + 1;
+    } else {
+      // alpha_k = q_k^T v ; v -= alpha_k q_k + beta_{k-1} q_{k-1}
+      CK(multi_dot(nd, nb, Q, ldq, k, k + 1, v, active, dpart, nchunk, dots, c->stream));
+      CK(lanczos_alpha(nb, k, nl, dots, active, c->alpha_d.as<double>(), c->beta_d.as<double>(),
+                       coef, c->stream));
+      CK(multi_axpy(nd, nb, Q, ldq, std::max(0, k - 1), k + 1, k > 0 ? coef : coef + 1, 2, v,
+                    active, c->stream));
+      if (c->opt.reorth) {
+        for (int pass = 0; pass < 2; ++pass) {
+          CK(multi_dot(nd, nb, Q, ldq, 0, k + 1, v, active, dpart, nchunk, dots, c->stream));
+          CK(multi_axpy(nd, nb, Q, ldq, 0, k + 1, dots, k + 1, v, active, c->stream));
+        }
+      }
+      // beta_k = ||v||, q_{k+1} = v / beta_k (with breakdown / early-exit tests)
+      CK(multi_dot(nd, nb, v, nd, 0, 1, v, active, dpart, nchunk, dots, c->stream));
+      CK(lanczos_beta(nb, k, nl, dots, active, c->alpha_d.as<double>(), c->beta_d.as<double>(),
+                      c->steps_d.as<int>(), c->lstate_d.as<double>(), c->opt.lanczos_rtol,
+                      c->opt.fkind, c->flags_d.as<int>(), c->stream));
+      CK(lanczos_next(nd, nb, k, nl, active, c->lstate_d.as<double>(), c->beta_d.as<double>(), v, Q,
+                      ldq, c->stream));
     }
-    // beta_k = ||v||, q_{k+1} = v / beta_k (with breakdown / early-exit tests)
-    CK(multi_dot(nd, nb, v, nd, 0, 1, v, active, dpart, nchunk, dots, c->stream));
-    CK(lanczos_beta(nb, k, nl, dots, active, c->alpha_d.as<double>(), c->beta_d.as<double>(),
-                    c->steps_d.as<int>(), c->lstate_d.as<double>(), c->opt.lanczos_rtol,
-                    c->opt.fkind, c->flags_d.as<int>(), c->stream));
-    CK(lanczos_next(nd, nb, k, nl, active, c->lstate_d.as<double>(), c->beta_d.as<double>(), v, Q,
-                    ldq, c->stream));
     CKS(timing_mark(c, 4));
     // stats and the number of probes still running
     std::vector<int> act(nb);
@@ -946,8 +1021,25 @@ static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const d
     if (any == 0) break;
   }
   CKS(timing_mark(c, 5));
-  CK(tridiag_f11(nb, nl, c->alpha_d.as<double>(), nl, c->beta_d.as<double>(), nl,
-                 c->steps_d.as<int>(), c->opt.fkind, c->dout_d.as<double>(), c->stream));
+  if (blk) {
+    CK(block_quadrature(nblk, bstart, bsz, bsteps, steps_done, nl, c->bA.as<double>(),
+                        c->bB.as<double>(), c->bT.as<double>(), c->bW.as<double>(),
+                        c->blam.as<double>(), ldT, ldl, c->bm.as<int>(), c->opt.fkind,
+                        c->dout_d.as<double>(), c->stream));
+    // per-slot step counts from the blocks
+    std::vector<int> bs(nblk), per(nb);
+    CK(cudaMemcpyAsync(bs.data(), bsteps, sizeof(int) * nblk, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int B = 0; B < nblk; ++B)
+      for (int l = 0; l < blk->sz[B]; ++l)
+        per[blk->start[B] + l] = bs[B] > 0 ? bs[B] : steps_done;
+    CK(cudaMemcpyAsync(c->steps_d.p, per.data(), sizeof(int) * nb, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  } else {
+    CK(tridiag_f11(nb, nl, c->alpha_d.as<double>(), nl, c->beta_d.as<double>(), nl,
+                   c->steps_d.as<int>(), c->opt.fkind, c->dout_d.as<double>(), c->stream));
+  }
   CKS(timing_mark(c, 6));
   CK(cudaMemcpyAsync(out.d, c->dout_d.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream));
   if (out.alpha)
@@ -980,7 +1072,58 @@ static rpa_status run_probes(rpa_ctx* c, long long count, const long long* probe
   const int nb_max = choose_batch(c, count);
   CKS(ensure_workspace(c, nb_max));
   const int nl = c->opt.lanczos_max;
+  const int bmax = c->opt.lanczos_block;
   *nonconv = false;
+  if (bmax > 1) {
+    // blocks: runs of consecutive entries with one frequency and distinct points, at most
+    // bmax long; waves hold whole blocks
+    std::vector<long long> bstart;
+    for (long long i = 0; i < count;) {
+      long long j = i + 1;
+      while (j < count && j - i < bmax && omg[j] == omg[i]) {
+        bool dup = false;
+        for (long long q = i; q < j; ++q) dup = dup || probe[q] == probe[j];
+        if (dup) break;
+        ++j;
+      }
+      bstart.push_back(i);
+      i = j;
+    }
+    bstart.push_back(count);
+    const int wave_cap = std::max(nb_max, bmax);
+    size_t bi = 0;
+    while (bi + 1 < bstart.size()) {
+      const long long s0 = bstart[bi];
+      size_t be = bi + 1;
+      while (be + 1 < bstart.size() && bstart[be + 1] - s0 <= wave_cap) ++be;
+      const int nb = (int)(bstart[be] - s0);
+      BlockLayout L;
+      L.first.resize(nb);
+      L.size.resize(nb);
+      for (size_t q = bi; q < be; ++q) {
+        const int f = (int)(bstart[q] - s0), n = (int)(bstart[q + 1] - bstart[q]);
+        L.start.push_back(f);
+        L.sz.push_back(n);
+        for (int l = 0; l < n; ++l) {
+          L.first[f + l] = f;
+          L.size[f + l] = n;
+        }
+      }
+      if (nb > nb_max) CKS(ensure_workspace(c, nb));
+      c->err.clear();
+      WaveOut o;
+      o.d = d + s0;
+      o.alpha = nullptr;  // no scalar tridiagonal in block mode
+      o.beta = nullptr;
+      o.steps = steps ? steps + s0 : nullptr;
+      if (alpha) std::memset(alpha + s0 * nl, 0, sizeof(double) * nb * nl);
+      if (beta) std::memset(beta + s0 * nl, 0, sizeof(double) * nb * nl);
+      CKS(run_wave(c, nb, probe + s0, omg + s0, o, st, &L));
+      if (!c->err.empty()) *nonconv = true;
+      bi = be;
+    }
+    return RPA_OK;
+  }
   for (long long s0 = 0; s0 < count; s0 += nb_max) {
     const int nb = (int)std::min<long long>(nb_max, count - s0);
     c->err.clear();
@@ -1104,6 +1247,7 @@ rpa_status rpa_default_options(rpa_options* o) {
   o->inner_tol = 0.0;
   o->tile = -1;
   o->graphs = 1;
+  o->lanczos_block = 1;
   return RPA_OK;
 }
 
@@ -1383,6 +1527,10 @@ rpa_status rpa_set_options(rpa_ctx* c, const rpa_options* o) {
     return fail(c, RPA_EINVAL, "bad tile option");
   }
   if (o->graphs != 0 && o->graphs != 1) return fail(c, RPA_EINVAL, "bad graphs option");
+  if (o->lanczos_block < 1 || o->lanczos_block > block_max())
+    return fail(c, RPA_EINVAL, "lanczos_block out of range");
+  if (o->lanczos_block > 1 && (o->lanczos_rtol != 0.0 || !o->reorth))
+    return fail(c, RPA_EINVAL, "block Lanczos needs full reorthogonalisation and no early exit");
   const bool realloc = o->precision != c->opt.precision || o->lanczos_max != c->opt.lanczos_max ||
                        o->refine != c->opt.refine;
   c->opt = *o;

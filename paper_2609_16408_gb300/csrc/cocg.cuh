@@ -102,5 +102,28 @@ cudaError_t multi_axpy(long long nd, int nb, const double* Q, long long ldq, int
 cudaError_t convert_d2f(const double* a, float* b, long long n, cudaStream_t s);
 cudaError_t convert_f2d(const float* a, double* b, long long n, cudaStream_t s);
 cudaError_t jacobi_eig(double* a, double* v, double* lam, int n, cudaStream_t s);
+cudaError_t jacobi_eig_batched(double* a, double* v, double* lam, const int* n, int count,
+                               long long lda, long long ldl, cudaStream_t s);
+// block Lanczos quadrature (lanczos_block.cu)
+int block_max();
+cudaError_t block_dot(long long nd, int nslot, int bmax, const int* bfirst, const int* bsize,
+                      const double* Q, long long ldq, long long ldj, int j0, int nj,
+                      const double* V, const int* active, double* part, int nchunk, double* D,
+                      cudaStream_t s);
+cudaError_t block_axpy(long long nd, int nslot, const int* bfirst, const int* bsize,
+                       const double* Q, long long ldq, int nj, const double* D, int ldD,
+                       double* V, const int* active, cudaStream_t s);
+cudaError_t block_store_a(int nblk, const int* bstart, const int* bsz, const double* D, int ldD,
+                          int nj, int k, int nl, double* Ab, const int* active, cudaStream_t s);
+cudaError_t block_chol(int nblk, const int* bstart, const int* bsz, const double* G, int ldG,
+                       int pass, int k, int nl, const double* Ab, double* Rk, double* Rinv,
+                       double* Bb, int* active, int* bsteps, cudaStream_t s);
+cudaError_t block_scale(long long nd, int nblk, const int* bstart, const int* bsz,
+                        const double* Rinv, const double* V, double* out, long long ldo,
+                        const int* active, cudaStream_t s);
+cudaError_t block_quadrature(int nblk, const int* bstart, const int* bsz, const int* bsteps,
+                             int steps_all, int nl, const double* Ab, const double* Bb, double* T,
+                             double* W, double* lam, long long ldT, long long ldl, int* mdim,
+                             int fkind, double* dout, cudaStream_t s);
 
 }  // namespace rpa

@@ -339,7 +339,7 @@ cudaError_t convert_f2d(const float* a, double* b, long long n, cudaStream_t s) 
 // cyclic Jacobi eigen-decomposition of a small symmetric matrix (one block); a is n x n
 // row-major and is overwritten; v receives eigenvectors as columns; lam the eigenvalues.
 // -------------------------------------------------------------------------------------------
-__global__ void k_jacobi(double* a, double* v, double* lam, int n) {
+__device__ void jacobi_body(double* a, double* v, double* lam, int n) {
   __shared__ double s_c, s_s, s_red[32];
   __shared__ int s_skip, s_done;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) v[e] = ((e / n) == (e % n)) ? 1.0 : 0.0;
@@ -409,6 +409,24 @@ __global__ void k_jacobi(double* a, double* v, double* lam, int n) {
       }
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = a[i * n + i];
+}
+
+__global__ void k_jacobi(double* a, double* v, double* lam, int n) { jacobi_body(a, v, lam, n); }
+
+// one matrix per block: matrix b of order n[b] at a + b * lda (eigenvectors likewise), its
+// eigenvalues at lam + b * ldl
+__global__ void k_jacobi_batched(double* a, double* v, double* lam, const int* n, long long lda,
+                                 long long ldl) {
+  const long long b = blockIdx.x;
+  jacobi_body(a + b * lda, v + b * lda, lam + b * ldl, n[b]);
+}
+
+cudaError_t jacobi_eig_batched(double* a, double* v, double* lam, const int* n, int count,
+                               long long lda, long long ldl, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_jacobi_batched<<<count, 256, 0, s>>>(a, v, lam, n, lda, ldl);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t jacobi_eig(double* a, double* v, double* lam, int n, cudaStream_t s) {

@@ -187,6 +187,35 @@ def test_chi0_mixed_double_float_residual(name):
         assert np.max(np.abs(r[i] - ref)) <= 1e-5 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("name,b", [("per", 3), ("dir", 4), ("mix", 2)])
+def test_block_lanczos_vs_oracle(name, b):
+    """Block Lanczos quadrature (probe-points of one frequency grouped into blocks of up to b,
+    a shorter block where the frequency changes) against the oracle's block recurrence."""
+    s = sysfix(name)
+    nl = 4
+    c, om, w = ctx_for(s, precision="fp64", lanczos_max=nl, stern_tol=1e-12, stern_maxit=5000,
+                       lanczos_block=b)
+    rng = np.random.default_rng(30 + b)
+    probes = np.concatenate([rng.choice(s.N_d, size=b + 1, replace=False),
+                             rng.choice(s.N_d, size=2, replace=False)]).astype(np.int64)
+    freqs = np.array([1] * (b + 1) + [3, 3], dtype=np.int32)
+    out = R.rpa_probe_density(c.ctx, probes, freqs, nl=nl)
+    # the grouping rule: consecutive entries of one frequency, at most b per block
+    groups = [list(range(0, b)), [b], [b + 1, b + 2]]
+    for g in groups:
+        ref = oracle.block_lanczos(s, probes[g], om[freqs[g[0]]], nl, tol=1e-12)
+        assert np.max(np.abs(out["d"][g] - ref["d"])) <= 1e-9, (g, out["d"][g], ref["d"])
+
+
+def test_block_lanczos_option_checked():
+    s = sysfix("per")
+    c, _, _ = ctx_for(s, precision="fp64")
+    with pytest.raises(RuntimeError):
+        R.rpa_set_options(c.ctx, lanczos_block=9)
+    with pytest.raises(RuntimeError):
+        R.rpa_set_options(c.ctx, lanczos_block=2, lanczos_rtol=1e-6)
+
+
 def test_tridiag_and_gl():
     rng = np.random.default_rng(5)
     for k in (1, 2, 3, 7, 20, 40):
