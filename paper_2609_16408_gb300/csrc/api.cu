@@ -1000,7 +1000,6 @@ static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const d
     CK(cudaMemcpyAsync(act.data(), active, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (st) {
-      st->matvecs += 0;  // counted below from probe activity
       st->solves += ss.solves;
       st->cocg_iters += ss.iters;
       st->refine_rounds += ss.refine_rounds;
@@ -1013,11 +1012,9 @@ static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const d
     if (ss.nonconv) c->err = "a Sternheimer solve reached stern_maxit";
     int any = 0;
     for (int b = 0; b < nb; ++b) any += act[b];
+    // one matrix-vector product per probe-point that ran this step
     if (st) st->matvecs += (long long)(ss.solves / std::max(1, c->ns));
-    if (ss.nonconv || ss.breakdown) {
-      // record and continue: results are still produced; the caller sees the status
-      c->opt.batch = c->opt.batch;  // no-op, keeps the state explicit
-    }
+    // a non-converged or broken-down solve is recorded in c->err; the step's results stand
     if (any == 0) break;
   }
   CKS(timing_mark(c, 5));
