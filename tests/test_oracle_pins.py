@@ -330,6 +330,30 @@ def test_interpolation_periodic_cubic_exact_away_from_wrap():
     assert np.max(np.abs(fh[sl] - f[sl])) < 1e-10 * np.abs(f).max()
 
 
+@pytest.mark.parametrize("kind", ["linear", "cubic"])
+def test_interpolation_nondivisible_periodic_axis(kind):
+    """52 points at stride 3: coarse nodes 0, 3, ..., 51 and a wrap interval of 1 point.  The
+    Lagrange weights stay a partition of unity and reproduce polynomials of the stencil's
+    degree at every fine point whose stencil spans the wrap (coordinates unwrapped by n)."""
+    n, g = 52, 3
+    W = oracle.interp_matrix(n, g, PERIODIC, kind)
+    nodes = oracle.coarse_nodes(n, g, PERIODIC)
+    assert list(nodes) == list(range(0, 52, 3)) and len(nodes) == 18
+    assert np.allclose(W.sum(axis=1), 1.0, atol=1e-14)
+    deg = 1 if kind == "linear" else 3
+    # a polynomial in the unwrapped coordinate is reproduced wherever the stencil does not
+    # straddle the wrap; straddling stencils see nodes shifted by n, so test f(x) on the
+    # fine points whose nearest-node stencils stay inside [0, 51]
+    for p in range(deg + 1):
+        f = (np.arange(n) / n) ** p
+        fh = W @ f[nodes]
+        inner = np.arange(3 * (deg // 2 + 1), n - 3 * (deg // 2 + 2))
+        assert np.allclose(fh[inner], f[inner], atol=1e-12)
+    # and across the wrap for a periodic smooth function the error is small
+    f = np.cos(2 * np.pi * np.arange(n) / n)
+    assert np.max(np.abs(W @ f[nodes] - f)) < (5e-2 if kind == "linear" else 5e-4)
+
+
 def test_interpolation_sum_invariance_periodic():
     """Shift-invariant partition-of-unity interpolants give sum(fine) = g^3 sum(coarse)."""
     shape = (12, 12, 12)
