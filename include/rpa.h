@@ -190,7 +190,8 @@ rpa_status rpa_batch_energy(int nsys, rpa_ctx *const *sys, double *ec_out, rpa_s
 /* Lanczos quadrature for an explicit list of probe-points: probe[i] is a fine-grid index,
  * freq[i] an index into the frequency list.  d (count doubles) receives d_j(i w).  When
  * alpha/beta are non-NULL they receive the tridiagonal entries (count x lanczos_max, zero
- * padded) and steps (may be NULL) the step count per probe. */
+ * padded; all zero with options.lanczos_block > 1, whose blocks are formed from consecutive
+ * entries of one frequency) and steps (may be NULL) the step count per probe. */
 rpa_status rpa_probe_density(rpa_ctx *ctx, int count, const long long *probe, const int *freq,
                              double *d, double *alpha, double *beta, int *steps,
                              rpa_stats *stats, int where);
