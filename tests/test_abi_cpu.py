@@ -51,3 +51,37 @@ def test_invalid_arguments_rejected_on_host():
     assert lib.rpa_create(C.byref(out), C.byref(g), None) == R.RPA_EINVAL
     assert lib.rpa_tridiag_f11(1, 0, None, None, 0, None) == R.RPA_EINVAL
     assert lib.rpa_gl_frequencies(0, None, None) == R.RPA_EINVAL
+
+
+def test_ctypes_structs_match_the_c_header(tmp_path):
+    """The binding's Grid / Options / Stats mirror rpa_grid / rpa_options / rpa_stats field by
+    field: sizes and offsets from a host C compilation of include/rpa.h."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no host C compiler")
+    inc = os.path.join(os.path.dirname(R.__file__), "..", "include")
+    structs = {"rpa_grid": R.Grid, "rpa_options": R.Options, "rpa_stats": R.Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rpa.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-x", "c", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln.strip():
+            cname, key, val = ln.split()
+            got[(cname, key)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
