@@ -85,3 +85,19 @@ def test_ctypes_structs_match_the_c_header(tmp_path):
         assert got[(cname, "size")] == C.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_binding_argument_counts_match_prototypes():
+    """Every declared entry point is bound with as many arguments as its C prototype."""
+    import os
+    txt = open(os.path.join(os.path.dirname(R.__file__), "..", "include", "rpa.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    lib = R.load()
+    for name in R.header_symbols():
+        m = re.search(r"\b" + name + r"\s*\(([^)]*)\)\s*;", txt)
+        assert m, name
+        params = [p for p in m.group(1).split(",") if p.strip() and p.strip() != "void"]
+        fn = getattr(lib, name)
+        if fn.argtypes is None:
+            continue  # not called through the binding
+        assert len(fn.argtypes) == len(params), (name, len(fn.argtypes), len(params))
