@@ -724,7 +724,8 @@ static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv_all, int maxit) {
   return RPA_OK;
 }
 
-// FP64 form: Galerkin guess, COCG, true-residual recheck with restart (as in the oracle).
+// FP64 form: Galerkin guess, COCG, true-residual recheck at exit with a restart while it is
+// above the tolerance.
 static rpa_status solve_fp64(rpa_ctx* c, int nb, const double* u, const int* active,
                              SolveStats& ss) {
   const int S = nb * c->ns;
