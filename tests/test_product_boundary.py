@@ -36,3 +36,20 @@ def test_library_does_not_link_the_oracle():
     if nm.returncode != 0:
         return
     assert "orc_" not in nm.stdout
+
+
+def test_missing_cuda_library_fails_loudly(tmp_path):
+    """Without a built library and without a CUDA compiler the binding raises instead of
+    falling back to anything else."""
+    code = (
+        "import os, sys; sys.path.insert(0, %r)\n"
+        "import paper_2609_16408_gb300 as R\n"
+        "R._BUILD = %r; R._SO = os.path.join(R._BUILD, 'librpa.so'); R._LIB = None\n"
+        "os.environ['NVCC'] = '/nonexistent/nvcc'\n"
+        "try:\n"
+        "    R.load()\n"
+        "    print('loaded')\n"
+        "except Exception as e:\n"
+        "    print('raised', type(e).__name__)\n" % (ROOT, str(tmp_path)))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert out.stdout.strip().startswith("raised"), out.stdout + out.stderr[-2000:]
