@@ -11,7 +11,8 @@ Pieces:
     Sternheimer/COCG solves with Galerkin initial guess, Lanczos quadrature per probe,
     tridiagonal f(T)_{11}, Gauss-Legendre frequencies.
   * this module: ctypes marshalling, coarse-grid selection and interpolation (Section 3.2),
-    the frequency/probe driver of Algorithm 1, the error metrics of Section 5.2.
+    the frequency/probe driver of Algorithm 1, the error metrics of Section 5.2, and the
+    block Lanczos quadrature (numpy block recurrence over the C oracle's operator).
   * ``dense.py``: the exact target on tiny grids from the sum-over-states response (Eq. 2).
 
 Parity status of each function (what pins it) is listed in the test-suite
