@@ -286,7 +286,8 @@ void orc_nu_half(const orc_sys *s, int count, const double *q, double *u) {
  * COCG uses the unconjugated bilinear form a^T b; it stops when the recursive residual
  * satisfies ||r||_2 <= tol ||b||_2 and then re-checks the true residual, restarting from the
  * current iterate if the true residual is still above tol.  Returns iterations taken, or
- * -1 when maxit is exhausted.
+ * -1 when maxit is exhausted, or -2 when 50 restarts end with the true residual still
+ * above tol (the stopping rule of Section 4 was not met).
  * ------------------------------------------------------------------------------------- */
 static double norm2c(const cplx *a, long N) {
   double s = 0.0;
@@ -340,7 +341,10 @@ static int cocg_solve(const orc_sys *s, int n, double omega, const double *u, do
       for (long i = 0; i < N; ++i) p[i] = r[i] + beta * p[i];
     }
   }
-  return it;
+  /* every restart converged recursively but the true residual never met the tolerance */
+  orc_apply_h(s, x, sigma, w);
+  for (long i = 0; i < N; ++i) r[i] = b[i] - w[i];
+  return norm2c(r, N) <= tol * bn ? it : -2;
 }
 
 /* Galerkin initial guesses of all N_s systems for one u (Section 4):

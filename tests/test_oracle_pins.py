@@ -203,6 +203,96 @@ def test_lanczos_converges_to_exact_diagonal(tiny_exact):
     assert np.max(np.abs(d - dex[probes])) < 1e-9 * np.max(np.abs(dex))
 
 
+def _dense_lanczos(A, j, nl, rtol=0.0):
+    """Plain Lanczos on an explicit matrix (numpy, full reorthogonalisation, tridiagonal
+    eigen-solve by eigh), written from the recurrence of Section 3.1 independently of the C
+    oracle.  Stops at the first step k >= 2 with |d_k - d_{k-1}| <= rtol |d_k| (rtol > 0) or
+    when the next beta is <= 1e-14 |alpha_1| (Krylov space exhausted).  Returns
+    (alpha, beta, d per step, reason) with reason 'exit', 'breakdown' or 'steps'."""
+    N = A.shape[0]
+    Q = np.zeros((N, nl + 1))
+    Q[j, 0] = 1.0
+    al, be, ds = [], [], []
+    for k in range(nl):
+        v = A @ Q[:, k]
+        al.append(Q[:, k] @ v)
+        v -= al[k] * Q[:, k]
+        if k > 0:
+            v -= be[k - 1] * Q[:, k - 1]
+        for _ in range(2):
+            v -= Q[:, :k + 1] @ (Q[:, :k + 1].T @ v)
+        T = np.diag(al) + np.diag(be[:k], 1) + np.diag(be[:k], -1)
+        lam, W = np.linalg.eigh(T)
+        ds.append(float(W[0] ** 2 @ (np.log1p(-lam) + lam)))
+        if rtol > 0 and k >= 1 and abs(ds[k] - ds[k - 1]) <= rtol * abs(ds[k]):
+            return np.array(al), np.array(be), np.array(ds), "exit"
+        if k == nl - 1:
+            break
+        bn = float(np.linalg.norm(v))
+        if bn <= 1e-14 * abs(al[0]):
+            return np.array(al), np.array(be), np.array(ds), "breakdown"
+        be.append(bn)
+        Q[:, k + 1] = v / bn
+    return np.array(al), np.array(be), np.array(ds), "steps"
+
+
+@pytest.mark.parametrize("rtol", [0.95, 1e-1, 1e-4, 1e-7])
+def test_lanczos_early_exit_step_matches_dense_recurrence(tiny_exact, rtol):
+    """Early exit: the oracle stops at the first step k >= 2 with |d_k - d_{k-1}| <= rtol |d_k|
+    and returns d_k.  The step is taken from a plain Lanczos on the dense A; the three
+    tolerances give three different exit steps, so an off-by-one in the step index (testing
+    d_{k+1} against d_k, or starting the test at k = 3) fails; at rtol = 0.95 one probe exits
+    at the earliest allowed step, k = 2."""
+    s, omega, out = tiny_exact
+    A = out[0][3]
+    exits = set()
+    for j in (5, 60, 200):
+        al, be, ds, why = _dense_lanczos(A, j, 14, rtol=rtol)
+        assert why == "exit"
+        r = oracle.lanczos(s, np.array([j]), omega, nl=14, tol=1e-13, lrtol=rtol)
+        assert r["steps"][0] == len(ds)
+        assert abs(r["d"][0] - ds[-1]) <= 1e-9 * abs(ds[-1])
+        assert np.allclose(r["alpha"][0][:len(al)], al, rtol=1e-9, atol=1e-13)
+        exits.add(len(ds))
+    assert min(exits) >= 2
+    if rtol == 0.95:
+        assert min(exits) == 2
+
+
+def test_lanczos_breakdown_on_exhausted_krylov_space():
+    """Breakdown: on a six-point chain with one occupied state, the Krylov space of A from e_j
+    is all of R^6, so beta_6 vanishes and the recurrence must stop after exactly six steps
+    (checked against a plain dense Lanczos), where the Gauss rule is exact: d_j equals the
+    dense [f(A)]_jj.  The well sits off the grid points so that no mirror symmetry closes the
+    space earlier."""
+    s = synth.gaussian_system("chain6", (6, 1, 1), (3.3, 1.0, 1.0), (PERIODIC,) * 3,
+                              np.array([[1.234, 0.5, 0.5]]), np.array([1.5]), np.array([0.6]), 1,
+                              fd_radius=3, proj_sigma=None, seed=3, min_gap=0.0, cache=False)
+    H = s.dense_h()
+    lap = dense.dense_laplacian(s.n, s.h, s.bc,
+                                synth.systems.second_derivative_weights(s.fd_radius))
+    for omega in (0.4, 0.05):
+        dex, _, _, A, _, _ = dense.exact_diagonal(H, lap, s.ns, s.dV, omega)
+        for j in range(s.N_d):
+            al, be, ds, why = _dense_lanczos(A, j, 10)
+            assert why == "breakdown" and len(ds) == s.N_d
+            r = oracle.lanczos(s, np.array([j]), omega, nl=10, tol=1e-13)
+            assert r["steps"][0] == s.N_d
+            assert abs(r["d"][0] - dex[j]) <= 1e-12 * abs(dex[j])
+            assert np.allclose(r["alpha"][0][:s.N_d], al, rtol=1e-10, atol=1e-14)
+
+
+def test_cocg_reports_an_unmet_tolerance():
+    """A Sternheimer tolerance below FP64 rounding cannot be met by the true residual: after
+    its restarts the oracle's COCG must report failure instead of returning the iterate."""
+    s = tiny()
+    u = np.random.default_rng(0).standard_normal(s.N_d)
+    with pytest.raises(RuntimeError):
+        oracle.chi0(s, 0.3, u, tol=1e-18, maxit=10 ** 7)
+    r, it = oracle.chi0(s, 0.3, u, tol=1e-12)  # a reachable tolerance still succeeds
+    assert np.all(it > 0)
+
+
 def test_block_lanczos_single_probe_equals_scalar(tiny_exact):
     """A block of one probe is the scalar recurrence (independent code: C scalar Lanczos)."""
     s, omega, out = tiny_exact
