@@ -84,6 +84,7 @@ __global__ void k_gram_coef(int ns, int nchunk, const double* __restrict__ gpart
 }
 
 // x0[(b,n)][r] = sum_k psi_k(r) C_b[k][n]; output tile 64 points x 32 states for one b.
+// Point tiles run along gridDim.x (up to 2^31 - 1 tiles), (b, state tile) along gridDim.y.
 template <typename T>
 __global__ void __launch_bounds__(256) k_x0(long long nd, int ns, int nb,
                                             const T* __restrict__ psi,
@@ -94,9 +95,9 @@ __global__ void __launch_bounds__(256) k_x0(long long nd, int ns, int nb,
   __shared__ T sP[KK][TR];
   __shared__ cpx<T> sC[KK][TN];
   const int ntn = (ns + TN - 1) / TN;
-  const int b = blockIdx.x / ntn, nt = blockIdx.x - b * ntn;
+  const int b = blockIdx.y / ntn, nt = blockIdx.y - b * ntn;
   if (active && !active[b]) return;
-  const long long r0 = (long long)blockIdx.y * TR;
+  const long long r0 = (long long)blockIdx.x * TR;
   const int n0 = nt * TN;
   const int tr = threadIdx.x & 15, tn = threadIdx.x >> 4;  // 4 points x 2 states per thread
   cpx<T> acc[4][2];
@@ -153,7 +154,8 @@ cudaError_t galerkin_guess(long long nd, int ns, int nb, const T* psi, const dou
   k_gram<T><<<g1, 256, 0, s>>>(nd, ns, psi, u, probe_active, nchunk, chunk_len, gpart);
   dim3 g2((ns * ns + 255) / 256, nb);
   k_gram_coef<T><<<g2, 256, 0, s>>>(ns, nchunk, gpart, eps, omega, probe_active, dV, cmat);
-  dim3 g3(nb * ((ns + 31) / 32), (unsigned)((nd + 63) / 64));
+  if ((long long)nb * ((ns + 31) / 32) > 65535) return cudaErrorInvalidValue;
+  dim3 g3((unsigned)((nd + 63) / 64), nb * ((ns + 31) / 32));
   k_x0<T><<<g3, 256, 0, s>>>(nd, ns, nb, psi, cmat, probe_active, x0);
   note_launch(3);
   return cudaGetLastError();

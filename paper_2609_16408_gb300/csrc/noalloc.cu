@@ -26,19 +26,28 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
 
-// Device address of g_scratch on the current device (looked up once per device; in host
-// code the symbol itself is only a host-side stand-in and must not be passed to a kernel).
-cudaError_t scratch_address(void** out) {
+// Device address of g_scratch on the current device.  In host code the symbol itself is
+// only a host-side stand-in and must not be passed to a kernel.  The address is looked up
+// again on every call made outside a stream capture (so that a context torn down and
+// re-created since the last call cannot leave a stale address behind); during a capture,
+// where the lookup may not be legal, the address cached by the last uncaptured call on this
+// device is used, and a capture with no cached address is refused.
+cudaError_t scratch_address(cudaStream_t s, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_addr[dev] = p;
+  } else if (!g_scratch_addr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;
@@ -57,6 +66,8 @@ extern "C" rpa_status rpa_galerkin_noalloc(long long nd, int ns, const double* p
                                            void* cuda_stream) {
   if (nd < 1 || nd >= (1LL << 31) || ns < 1 || ns > 1024 || count < 0 || !(dV > 0.0))
     return RPA_EINVAL;
+  // the projection kernels take point tiles of 64 along gridDim.x (< 2^31 tiles) and state
+  // tiles of 32 along gridDim.y (<= 32 here): every nd and ns accepted above fits
   const int nchunk = chunks_for(nd);
   // the coefficient matrix starts on a 256-byte boundary after the Gram partials
   const size_t gram_bytes = (((size_t)nchunk * ns * ns * sizeof(double)) + 255) & ~(size_t)255;
@@ -64,12 +75,12 @@ extern "C" rpa_status rpa_galerkin_noalloc(long long nd, int ns, const double* p
   if (gram_bytes + coef_bytes > kScratchBytes) return RPA_EINVAL;  // beyond the scratch size
   if (count == 0) return RPA_OK;
   if (!psi || !eps || !omega || !u || !x0) return RPA_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   void* base = nullptr;
-  if (scratch_address(&base) != cudaSuccess) return RPA_ECUDA;
+  if (scratch_address(s, &base) != cudaSuccess) return RPA_ECUDA;
   double* gpart = static_cast<double*>(base);
   rpa::cpx<double>* cmat =
       reinterpret_cast<rpa::cpx<double>*>(static_cast<unsigned char*>(base) + gram_bytes);
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   // one probe at a time: the Gram kernel writes every partial it later sums, and the
   // coefficient kernel writes the whole matrix, so nothing in the scratch needs clearing
   for (int b = 0; b < count; ++b) {
