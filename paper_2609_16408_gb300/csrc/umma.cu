@@ -14,9 +14,12 @@
 //     (8-bit significand, relative rounding 2^-9).  The guess is then accurate to ~1e-2
 //     relative; COCG removes the difference, at the cost of some extra iterations.
 // Both forms use the same byte layout: a stage holds 128 bytes of K per row (32 tf32 or
-// 64 bf16).  Every mbarrier wait is bounded;
-// on expiry the kernel records an error code, waits (bounded) for its MMAs, frees TMEM and
-// returns.
+// 64 bf16).  Every mbarrier wait is bounded, and the block takes each wait's outcome
+// together (__syncthreads_and), so that all threads leave the pipeline at the same step.  On
+// expiry the kernel records an error code, waits (bounded, full limit) for the commit of the
+// last stage it issued -- which covers every MMA in flight -- frees TMEM and returns.  With
+// test_expire the first pipeline wait is made on a barrier nothing arrives on, with a short
+// limit, before any MMA is issued: the failure path can then be exercised without a fault.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -30,6 +33,7 @@ constexpr int kTK = 32;                       // tf32 K elements per shared-memo
 constexpr int kTK16 = 64;                     // bf16 K elements per stage (same bytes)
 constexpr uint32_t kTileBytes128 = 128 * kTK * 4;  // 128 rows x 128 bytes
 constexpr uint32_t kWaitLimit = 1u << 26;
+constexpr uint32_t kTestWaitLimit = 1u << 10;  // polls of the test_expire wait
 
 // byte offset of (row, k) in a K-major tile of 32 tf32 per row (core matrices 8 x 16 B;
 // LBO = 128 B between K-adjacent core matrices, SBO = 1024 B between 8-row groups)
@@ -89,9 +93,9 @@ template <bool BF16>
 __global__ void __launch_bounds__(128, 1)
     k_gram_tc(long long nd, int ns, const float* __restrict__ psi, const float* __restrict__ u,
               const int* __restrict__ active, int nchunk, long long chunk_len, int ntile_n,
-              int nN, double* __restrict__ gpart, int* __restrict__ err) {
+              int nN, double* __restrict__ gpart, int* __restrict__ err, int test_expire) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[3];  // [2]: test_expire only, never arrived on
   __shared__ uint32_t tmem_base;
   const int b = blockIdx.y;
   if (active && !active[b]) return;
@@ -102,6 +106,7 @@ __global__ void __launch_bounds__(128, 1)
   const long long r1 = min(r0 + chunk_len, nd);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t mb0 = umma::smem_addr(&mbar[0]), mb1 = umma::smem_addr(&mbar[1]);
+  const uint32_t mbx = umma::smem_addr(&mbar[2]);
   if (warp == 0) {
     umma::tmem_alloc(umma::smem_addr(&tmem_base), 128);
     umma::tmem_relinquish();
@@ -109,6 +114,7 @@ __global__ void __launch_bounds__(128, 1)
   if (threadIdx.x == 0) {
     umma::mbar_init(mb0, 1);
     umma::mbar_init(mb1, 1);
+    umma::mbar_init(mbx, 1);
     umma::mbar_fence_init();
   }
   umma::fence_before_sync();
@@ -121,10 +127,17 @@ __global__ void __launch_bounds__(128, 1)
   constexpr int TK = BF16 ? kTK16 : kTK;
   const int nsteps = (int)((span + TK - 1) / TK);
   bool ok = true;
-  for (int step = 0; step < nsteps && ok; ++step) {
+  int issued = 0;  // stages whose MMAs were issued and committed (block-uniform)
+  for (int step = 0; step < nsteps; ++step) {
     const int st = step & 1;
-    if (step >= 2) ok = umma::mbar_wait_bounded(st ? mb1 : mb0, ((step - 2) >> 1) & 1, kWaitLimit);
-    if (!ok) break;
+    if (step >= 2 || (test_expire && step == 0)) {
+      const bool w = (test_expire && step == 0)
+                         ? umma::mbar_wait_bounded(mbx, 0, kTestWaitLimit)
+                         : umma::mbar_wait_bounded(st ? mb1 : mb0, ((step - 2) >> 1) & 1,
+                                                   kWaitLimit);
+      ok = __syncthreads_and(w) != 0;
+      if (!ok) break;
+    }
     uint8_t* ahi = smem + st * (BF16 ? 2 : 4) * kTileBytes128;
     uint8_t* alo = ahi + kTileBytes128;
     uint8_t* bhi = BF16 ? alo : alo + kTileBytes128;
@@ -158,19 +171,21 @@ __global__ void __launch_bounds__(128, 1)
                     umma::smem_addr(blo), idesc, step == 0);
       umma::mma_commit(st ? mb1 : mb0);
     }
+    issued = step + 1;
   }
-  if (nsteps > 0) {
-    const int last = nsteps - 1;
+  if (issued > 0) {  // the last issued commit covers every MMA issued before it
+    const int last = issued - 1;
     const bool done = umma::mbar_wait_bounded((last & 1) ? mb1 : mb0, (last >> 1) & 1, kWaitLimit);
     ok = ok && done;
   }
+  ok = __syncthreads_and(ok) != 0;
   if (!ok && threadIdx.x == 0) atomicExch(err, 1);
   umma::fence_after_sync();
   double* out = gpart + ((long long)b * nchunk + c) * ns * ns;
   const int k = k0 + warp * 32 + lane;
   for (int j0 = 0; j0 < nN; j0 += 16) {
     float v[16];
-    if (nsteps > 0 && ok) {
+    if (issued > 0 && ok) {
       umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, v);
     } else {
 #pragma unroll
@@ -194,22 +209,23 @@ template <bool BF16>
 __global__ void __launch_bounds__(128, 1)
     k_x0_tc(long long nd, int ns, const float* __restrict__ psi, const cpx<float>* __restrict__ cmat,
             const int* __restrict__ active, int ntile_n, int nN, cpx<float>* __restrict__ x0,
-            int* __restrict__ err) {
+            int* __restrict__ err, int test_expire) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t mbar[1];
+  __shared__ __align__(8) uint64_t mbar[2];  // [1]: test_expire only, never arrived on
   __shared__ uint32_t tmem_base;
   const int b = blockIdx.y / ntile_n, nt = blockIdx.y - b * ntile_n;
   if (active && !active[b]) return;
   const long long r0 = (long long)blockIdx.x * 128;
   const int n0 = nt * 128;  // states n0 .. n0+127 -> columns 2(n - n0) + {0, 1}
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t mb = umma::smem_addr(&mbar[0]);
+  const uint32_t mb = umma::smem_addr(&mbar[0]), mbx = umma::smem_addr(&mbar[1]);
   if (warp == 0) {
     umma::tmem_alloc(umma::smem_addr(&tmem_base), 256);
     umma::tmem_relinquish();
   }
   if (threadIdx.x == 0) {
     umma::mbar_init(mb, 1);
+    umma::mbar_init(mbx, 1);
     umma::mbar_fence_init();
   }
   umma::fence_before_sync();
@@ -225,9 +241,15 @@ __global__ void __launch_bounds__(128, 1)
   const cpx<float>* cb = cmat + (long long)b * ns * ns;
   const int nsteps = (ns + TK - 1) / TK;
   bool ok = true;
-  for (int step = 0; step < nsteps && ok; ++step) {
-    if (step >= 1) ok = umma::mbar_wait_bounded(mb, (step - 1) & 1, kWaitLimit);
-    if (!ok) break;
+  int issued = 0;  // stages whose MMAs were issued and committed (block-uniform)
+  for (int step = 0; step < nsteps; ++step) {
+    if (step >= 1 || test_expire) {
+      const bool w = (test_expire && step == 0)
+                         ? umma::mbar_wait_bounded(mbx, 0, kTestWaitLimit)
+                         : umma::mbar_wait_bounded(mb, (step - 1) & 1, kWaitLimit);
+      ok = __syncthreads_and(w) != 0;
+      if (!ok) break;
+    }
     const int kb = step * TK;
     for (int e = threadIdx.x; e < 128 * TK; e += 128) {
       const int kk = e >> 7, row = e & 127;  // consecutive threads: consecutive points
@@ -262,17 +284,19 @@ __global__ void __launch_bounds__(128, 1)
                     umma::smem_addr(blo), idesc, step == 0);
       umma::mma_commit(mb);
     }
+    issued = step + 1;
   }
-  if (nsteps > 0) {
-    const bool done = umma::mbar_wait_bounded(mb, (nsteps - 1) & 1, kWaitLimit);
+  if (issued > 0) {  // the last issued commit covers every MMA issued before it
+    const bool done = umma::mbar_wait_bounded(mb, (issued - 1) & 1, kWaitLimit);
     ok = ok && done;
   }
+  ok = __syncthreads_and(ok) != 0;
   if (!ok && threadIdx.x == 0) atomicExch(err, 1);
   umma::fence_after_sync();
   const long long r = r0 + warp * 32 + lane;
   for (int j0 = 0; j0 < nN; j0 += 16) {
     float v[16];
-    if (ok) {
+    if (issued > 0 && ok) {
       umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, v);
     } else {
 #pragma unroll
@@ -312,7 +336,8 @@ static cudaError_t tc_attr() {
 cudaError_t galerkin_guess_tc(long long nd, int ns, int nb, const float* psi, const double* eps,
                               const double* omega, const float* u, const int* probe_active,
                               double dV, double* gpart, int nchunk, cpx<float>* cmat,
-                              cpx<float>* x0, int* err, cudaStream_t s, bool bf16) {
+                              cpx<float>* x0, int* err, cudaStream_t s, bool bf16,
+                              int test_expire) {
   cudaError_t e = bf16 ? tc_attr<true>() : tc_attr<false>();
   if (e != cudaSuccess) return e;
   const long long chunk_len = (nd + nchunk - 1) / nchunk;
@@ -321,20 +346,22 @@ cudaError_t galerkin_guess_tc(long long nd, int ns, int nb, const float* psi, co
   dim3 g1(nt * nt, nb, nchunk);
   if (bf16)
     k_gram_tc<true><<<g1, 128, 4 * kTileBytes128, s>>>(nd, ns, psi, u, probe_active, nchunk,
-                                                       chunk_len, nt, nN, gpart, err);
+                                                       chunk_len, nt, nN, gpart, err,
+                                                       test_expire);
   else
     k_gram_tc<false><<<g1, 128, 8 * kTileBytes128, s>>>(nd, ns, psi, u, probe_active, nchunk,
-                                                        chunk_len, nt, nN, gpart, err);
+                                                        chunk_len, nt, nN, gpart, err,
+                                                       test_expire);
   e = gram_coef<float>(ns, nb, nchunk, gpart, eps, omega, probe_active, dV, cmat, s);
   if (e != cudaSuccess) return e;
   const int nN2 = std::min(256, ((2 * ns + 15) / 16) * 16);
   dim3 g3((unsigned)((nd + 127) / 128), nb * nt);
   if (bf16)
     k_x0_tc<true><<<g3, 128, 3 * kTileBytes128, s>>>(nd, ns, psi, cmat, probe_active, nt, nN2, x0,
-                                                     err);
+                                                     err, test_expire);
   else
     k_x0_tc<false><<<g3, 128, 6 * kTileBytes128, s>>>(nd, ns, psi, cmat, probe_active, nt, nN2,
-                                                      x0, err);
+                                                      x0, err, test_expire);
   note_launch(3);
   return cudaGetLastError();
 }
