@@ -80,7 +80,12 @@ typedef struct {
   int lanczos_max;       /* N_l: matrix-vector products per probe (1..256) */
   double lanczos_rtol;   /* early exit when |d_k - d_{k-1}| <= rtol |d_k|, k >= 2; 0 = off */
   double stern_tol;      /* Sternheimer relative residual ||b - A x||_2 <= tol ||b||_2 */
-  int stern_maxit;       /* COCG iteration cap per solve (RPA_ENOCONV beyond) */
+  int stern_maxit;       /* COCG iteration cap per solve, counted over all refinement rounds
+                            (RPA_ENOCONV beyond).  Default 20000: the solves at the smallest
+                            frequencies grow with the cell and the tolerance (the iteration
+                            tables of Section 5.6 rise as omega -> 0); a 64-atom cell at tol
+                            1e-4 has needed several thousand, beyond an earlier default of
+                            2000 */
   int precision;         /* RPA_FP64, RPA_MIXED or RPA_MIXED_BF16 */
   int reorth;            /* 1: full reorthogonalisation of the Lanczos basis (2 passes) */
   int stride[3];         /* coarsening factor g per axis (C_g of Section 3.2) */
@@ -95,7 +100,10 @@ typedef struct {
                             candidate tilings on the first COCG solve of each precision and
                             keep the fastest), 0 = 32 x 8 column tiles, -2 = 64 x 8 tiles with
                             two x points per thread (mixed form, even nx), h > 0 = tiles of h
-                            full x rows (needs nx <= 64); RPA_EINVAL if it does not fit */
+                            full x rows (needs nx <= 64), -100 - h = bands of h full x rows with
+                            two points per thread and a multi-stage asynchronous copy pipeline
+                            (mixed form, even nx <= 64, h divides ny); RPA_EINVAL if it does not
+                            fit */
   int graphs;            /* 1: replay each chunk of fused COCG iterations as a captured CUDA
                             graph (default); 0: launch the kernels one by one */
   int lanczos_block;     /* 1: scalar Lanczos quadrature per probe (Section 3.1, default);
@@ -103,6 +111,18 @@ typedef struct {
                             of one frequency and distinct grid points share one block
                             recurrence (the block variant named as future work in Section 6);
                             needs reorth = 1 and lanczos_rtol = 0; no tridiagonal output */
+  int refine_restart;    /* mixed form, after each FP64 residual refinement: 0 = continue the
+                            FP32 COCG recurrence from its last direction with the true
+                            residual in place of the recursive one (a reliable update; the
+                            Krylov space built so far is kept; default) when the inner
+                            tolerance is >= 1e-3, else restart; 1 = always restart it from
+                            p = r */
+  int debug_expire_waits; /* tests only (default 0): 1 makes the first bounded wait of every
+                            block of the tensor-core projection kernels (mixed form) wait on a
+                            barrier that nothing arrives on, with a short limit, before any
+                            MMA is issued; the call then returns RPA_ETIMEOUT with the tensor
+                            memory freed and the context usable, so the bounded-wait failure
+                            path can be tested without a GPU fault */
 } rpa_options;
 
 typedef struct {
@@ -128,6 +148,9 @@ typedef struct {
                               0 = 32 x 8 column tiles, -2 = 64 x 8 two-point tiles, h > 0 =
                               full-row tiles of height h */
   int tile_rows_tail;      /* the same for launches over at most 32 systems */
+  long long nonconv_solves;   /* solves that ended above the tolerance (iteration cap, or
+                                 refinement rounds or restarts used up) */
+  long long breakdown_solves; /* solves that broke down (p^T A p = 0 or non-finite) */
 } rpa_stats;
 
 /* ---- context --------------------------------------------------------------------------- */
@@ -238,8 +261,10 @@ rpa_status rpa_galerkin(rpa_ctx *ctx, int count, const double *omega, const doub
  *   multiple of 256) + ns^2 x 16 bytes, e.g.
  *   35 x 128^2 x 8 + 128^2 x 16 = 4.85 MB for a 52^3 grid with 128 states.  Larger sizes are
  *   rejected with RPA_EINVAL before any work is queued.
- *   The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- *   make that first call before any stream capture.  The call allocates nothing (no
+ *   Every call made outside a stream capture looks up the array's device address
+ *   (cudaGetSymbolAddress) on the current device; a call inside a capture reuses the address
+ *   of the last uncaptured call on that device (RPA_ECUDA if there was none), so make one
+ *   call before any stream capture.  The call allocates nothing (no
  *   cudaMalloc, no cudaFree).  Every call shares the scratch array and leaves its contents
  *   behind; calls whose work overlaps on the GPU (different streams, or host threads
  *   without ordering) race on it and must be serialised by the caller. */

@@ -63,6 +63,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = os.environ.get("NVCC", "nvcc")
     common = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-I" + os.path.join(_ROOT, "include")]
+    # extra compile definitions for variant builds, e.g. RPA_NVCC_FLAGS=-DRPA_DOT_F64=1
+    common += os.environ.get("RPA_NVCC_FLAGS", "").split()
 
     def compile_one(src):
         obj = os.path.join(_BUILD, os.path.basename(src)[:-3] + ".o")
@@ -96,7 +98,8 @@ class Options(C.Structure):
                 ("stride", C.c_int * 3), ("interp", C.c_int), ("batch", C.c_int),
                 ("fkind", C.c_int), ("refine", C.c_int), ("inner_tol", C.c_double),
                 ("profile", C.c_int), ("tile", C.c_int), ("graphs", C.c_int),
-                ("lanczos_block", C.c_int)]
+                ("lanczos_block", C.c_int), ("refine_restart", C.c_int),
+                ("debug_expire_waits", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -107,7 +110,8 @@ class Stats(C.Structure):
                 ("lanczos_steps_max", C.c_int), ("kernel_seconds", C.c_double * 8),
                 ("kernel_launches", C.c_longlong * 8), ("kernel_bytes", C.c_double * 8),
                 ("precision_bytes", C.c_int), ("tile_rows", C.c_int),
-                ("tile_rows_tail", C.c_int)]
+                ("tile_rows_tail", C.c_int), ("nonconv_solves", C.c_longlong),
+                ("breakdown_solves", C.c_longlong)]
 
     def as_dict(self):
         return dict(seconds_total=self.seconds_total, seconds_phase=list(self.seconds_phase),
@@ -119,7 +123,8 @@ class Stats(C.Structure):
                     kernel_launches=list(self.kernel_launches),
                     kernel_bytes=list(self.kernel_bytes),
                     precision_bytes=self.precision_bytes, tile_rows=self.tile_rows,
-                    tile_rows_tail=self.tile_rows_tail)
+                    tile_rows_tail=self.tile_rows_tail, nonconv_solves=self.nonconv_solves,
+                    breakdown_solves=self.breakdown_solves)
 
 
 def _declare(lib):
@@ -407,17 +412,56 @@ def rpa_galerkin(ctx, omega, u, ns):
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
+def _noalloc_check(psi, eps, omega, u, x0, stream):
+    """Argument checks of rpa_galerkin_noalloc, all before the C call: the kernels take raw
+    pointers and sizes, so a wrong dtype, shape, layout or device would make them read or
+    write past the caller's buffers."""
+    import torch
+    args = dict(psi=psi, eps=eps, omega=omega, u=u, x0=x0)
+    for k, t in args.items():
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"rpa_galerkin_noalloc: {k} must be a torch tensor")
+    for k in ("psi", "eps", "omega", "u"):
+        if args[k].dtype != torch.float64:
+            raise ValueError(f"rpa_galerkin_noalloc: {k} must be float64, got {args[k].dtype}")
+    if x0.dtype != torch.complex128:
+        raise ValueError(f"rpa_galerkin_noalloc: x0 must be complex128, got {x0.dtype}")
+    if psi.dim() != 2 or u.dim() != 2 or eps.dim() != 1 or omega.dim() != 1 or x0.dim() != 3:
+        raise ValueError("rpa_galerkin_noalloc: expected psi (ns, nd), eps (ns,), omega (count,), "
+                         "u (count, nd), x0 (count, ns, nd)")
+    ns, nd = int(psi.shape[0]), int(psi.shape[1])
+    count = int(u.shape[0])
+    want = dict(eps=(ns,), omega=(count,), u=(count, nd), x0=(count, ns, nd))
+    for k, shp in want.items():
+        if tuple(args[k].shape) != shp:
+            raise ValueError(f"rpa_galerkin_noalloc: {k} has shape {tuple(args[k].shape)}, "
+                             f"expected {shp}")
+    for k, t in args.items():
+        if not t.is_contiguous():
+            raise ValueError(f"rpa_galerkin_noalloc: {k} must be contiguous")
+    dev = psi.device
+    for k, t in args.items():
+        if not t.is_cuda or t.device != dev:
+            raise ValueError(f"rpa_galerkin_noalloc: {k} must be a CUDA tensor on {dev}")
+    if dev.index != torch.cuda.current_device():
+        raise ValueError("rpa_galerkin_noalloc: the tensors must live on the current device")
+    if stream is not None and getattr(stream, "device", dev) != dev:
+        raise ValueError("rpa_galerkin_noalloc: the stream belongs to another device")
+
+
 def rpa_galerkin_noalloc(psi, eps, dV, omega, u, x0, stream=None):
     """FP64 Galerkin guesses for callers that cannot allocate device memory.
 
-    All arguments are CUDA tensors owned by the caller: psi (ns, nd) float64, eps (ns,),
-    omega (count,), u (count, nd) float64, x0 (count, ns, nd) complex128 output.  Work is
-    queued on `stream` (a torch.cuda.Stream or None for the current stream) without
-    synchronising.  Uses a fixed 8 MiB device scratch array inside the library; sizes beyond
-    it raise RpaError(RPA_EINVAL)."""
+    All arguments are contiguous CUDA tensors on the current device, owned by the caller:
+    psi (ns, nd) float64, eps (ns,) float64, omega (count,) float64, u (count, nd) float64,
+    x0 (count, ns, nd) complex128 output; anything else raises ValueError before any work is
+    queued.  Work is queued on `stream` (a torch.cuda.Stream or None for the current stream)
+    without synchronising.  Uses a fixed 8 MiB device scratch array inside the library; sizes
+    beyond it raise RpaError(RPA_EINVAL)."""
     import torch
+    _noalloc_check(psi, eps, omega, u, x0, stream)
     ns, nd = int(psi.shape[0]), int(psi.shape[1])
-    count = int(u.shape[0]) if u.dim() == 2 else 1
+    count = int(u.shape[0])
     nchunk = min(256, max(1, (nd + 4095) // 4096))
     need = ((nchunk * ns * ns * 8 + 255) // 256) * 256 + ns * ns * 16
     st = stream if stream is not None else torch.cuda.current_stream()

@@ -109,9 +109,27 @@ struct rpa_ctx {
   };
   std::vector<ChunkGraph> graphs;
   int prof_cpx_bytes = 0;
+  // non-fatal outcome of the current call (results are still written): RPA_ENOCONV or
+  // RPA_EBREAKDOWN (the more severe is kept), with its reason
+  rpa_status soft = RPA_OK;
+  std::string soft_msg;
 };
 
 namespace rpa {
+// record a non-fatal outcome of the current call (EBREAKDOWN outranks ENOCONV)
+static void note_soft(rpa_ctx* c, rpa_status st, const char* msg) {
+  if (c->soft == RPA_OK || (st == RPA_EBREAKDOWN && c->soft == RPA_ENOCONV)) {
+    c->soft = st;
+    c->soft_msg = msg;
+  }
+}
+// the call's result: OK, or its recorded non-fatal status with the reason in last_error
+static rpa_status soft_status(rpa_ctx* c) {
+  const rpa_status st = c->soft;
+  if (st == RPA_OK) return RPA_OK;
+  c->soft = RPA_OK;
+  return fail(c, st, c->soft_msg);
+}
 rpa_status fail(rpa_ctx* c, rpa_status st, const std::string& msg) {
   if (c) c->err = msg;
   return st;
@@ -469,6 +487,8 @@ static CocgView<T> make_view(rpa_ctx* c, int nb, const T* u, cpx<T>* x, cpx<T>* 
 }
 
 constexpr int kChunkIters = 4;
+// smallest FP32 inner tolerance per refinement round at which the recurrence is continued
+constexpr double kContinueMinInnerTol = 1e-3;
 // Sternheimer tolerances at or above this use the double-float refinement residual
 constexpr double kDfResidualTol = 1e-8;
 static_assert(kChunkIters <= kChunkItersMax, "counts buffer holds one slot per iteration");
@@ -492,6 +512,7 @@ static FusedBufs<T> make_fused(rpa_ctx* c) {
   fb.nact = 0;
   fb.cd_in_smem = (sizeof(cpx<T>) * c->ngroup * kProjChunk <= 32768) ? 1 : 0;
   fb.row_ty = 0;
+  fb.band_ty = 0;
   return fb;
 }
 
@@ -500,9 +521,11 @@ static FusedBufs<T> make_fused(rpa_ctx* c) {
 template <typename T>
 static void set_tiling(const rpa_ctx* c, FusedBufs<T>& fb, int ty, int nact) {
   fb.row_ty = ty;
-  fb.ntiles_xy = ty > 0 ? (c->grid.n[1] + ty - 1) / ty
-                        : (ty == kTileX2 ? x2_tiles_xy(c->grid.n[0], c->grid.n[1])
-                                         : fused_ntiles_xy(c));
+  fb.band_ty = is_band(ty) ? band_rows(ty) : 0;
+  fb.ntiles_xy = is_band(ty) ? c->grid.n[1] / band_rows(ty)
+                 : ty > 0    ? (c->grid.n[1] + ty - 1) / ty
+                             : (ty == kTileX2 ? x2_tiles_xy(c->grid.n[0], c->grid.n[1])
+                                              : fused_ntiles_xy(c));
   const int nz = c->grid.n[2], R = c->grid.fd_radius;
   const int base = fused_zchunk(c);
   const long long want = 6LL * std::max(1, c->nsm);
@@ -534,10 +557,16 @@ static rpa_status choose_tiling(rpa_ctx* c, const CocgView<T>& cv, const FusedBu
     return RPA_OK;
   }
   if (c->tuned_ty[k][0] == -1) {
-    int cand[18];
+    int cand[26];
     int nc = 0;
     cand[nc++] = 0;
     if (sizeof(T) == 4 && x2_tile_fits(c->grid.n[0], c->grid.fd_radius)) cand[nc++] = kTileX2;
+    if (sizeof(T) == 4) {
+      int bty[8];
+      const int nb = band_candidates(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, c->ngroup,
+                                     bty, 8);
+      for (int i = 0; i < nb; ++i) cand[nc++] = band_code(bty[i]);
+    }
     nc += row_candidates<T>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, c->ngroup, cand + nc,
                             16);
     int best_ty[2] = {0, 0};
@@ -609,6 +638,7 @@ static rpa_status run_chunk_graph(rpa_ctx* c, const CocgView<T>& cv, const Fused
     }
   if (!hit) {
     if (fb.row_ty > 0) CK(launch_dirmatvec_rows_prepare<T>());  // attributes before capture
+    if (is_band(fb.row_ty)) CK(launch_dirmatvec_band_prepare());
     if (c->graphs.size() >= 64) {  // bounded cache: drop the oldest
       if (c->graphs.front().exec) cudaGraphExecDestroy(c->graphs.front().exec);
       c->graphs.erase(c->graphs.begin());
@@ -643,16 +673,19 @@ static rpa_status run_chunk_graph(rpa_ctx* c, const CocgView<T>& cv, const Fused
 }
 
 // COCG iterations until no system is active.  Expects r (and x) set for the active systems;
-// forms the projector coefficients of r, then iterates the fused kernels.
+// forms the projector coefficients of r, then iterates the fused kernels.  With cont, the
+// recurrence continues from the direction kept in p (and its projector coefficients in cp)
+// with the beta each system holds, instead of starting from p = r.
 template <typename T>
-static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv_all, int maxit) {
+static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv_all, int maxit, bool cont = false) {
   int cnt[kNumStatus];
   int done_iters = 0;
   const bool prof = c->opt.profile && c->have_pev && c->prof_stats;
   FusedBufs<T> fb = make_fused<T>(c);
   CK(proj_dots<T>(cv_all.nl, cv_all.nd, cv_all.nsys, cv_all.r, cv_all.sysi, 1 << kActive, fb.cr,
                   c->stream));
-  CK(fused_prepare<T>(cv_all, fb, c->stream));
+  CK(fused_prepare<T>(cv_all, fb, c->stream, cont ? 0 : 1));
+  if (cont) fb.first = 0;
   // launches cover only the active systems, listed at every chunk boundary
   CocgView<T> cv = cv_all;
   cv.list = c->list_d.as<int>();
@@ -780,7 +813,8 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
   CK(galerkin_guess_tc(c->nd, c->ns, nb, c->d32.psi.as<float>(), c->eps_d.as<double>(),
                        c->pomega_d.as<double>(), u32, active, c->dV, c->gpart.as<double>(),
                        gram_chunks(c->nd), c->cmat.as<cpx<float>>(), x, c->flags_d.as<int>() + 2,
-                       c->stream, c->opt.precision == RPA_MIXED_BF16));
+                       c->stream, c->opt.precision == RPA_MIXED_BF16,
+                       c->opt.debug_expire_waits));
   CK(set_status(S, c->ns, active, kActive, c->sysi.as<int>(), c->stream));
   CK(proj_dots<float>(cv.nl, c->nd, S, x, cv.sysi, 1 << kActive, cv.cdot, c->stream));
   CK((cocg_resid<float, float>(cv, x, r, p, 1 << kActive, nullptr, nullptr, nullptr, c->stream)));
@@ -801,23 +835,49 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
   CK(convert_f2d(u32, c->u64.as<double>(), (long long)nb * c->nd, c->stream));
   CocgView<double> cv64 = make_view<double>(c, nb, c->u64.as<double>(), x64, r64, nullptr,
                                             nullptr);
+  // Each round replaces the FP32 recursive residual by the FP64 true residual.  By default
+  // the FP32 recurrence then continues from its last direction (a reliable update: the
+  // Krylov space built so far is kept) as long as a round reduces the residual by at most
+  // kContinueMinInnerTol: deeper FP32 rounds leave rounding in the kept direction that is
+  // large next to the new residual, and the continued recurrence stalls (measured at an
+  // inner tolerance of 1e-5).  Otherwise, or with refine_restart = 1, each round restarts
+  // from p = r.
+  const bool cont = c->opt.refine_restart == 0 && itol >= kContinueMinInnerTol;
+  bool rounds_left = false;  // the last round ran: its corrections are not checked yet
   for (int round = 1; round <= c->opt.refine; ++round) {
+    rounds_left = false;
     CK(proj_dots<double>(cv64.nl, c->nd, S, x64, cv64.sysi, 1 << kConverged, cv64.cdot,
                          c->stream));
     // double-float residual while its ~2^-48 rounding stays far below the tolerance
     CK((cocg_resid<double, float>(cv64, x64, r64, nullptr, 1 << kConverged, r, p, x, c->stream,
-                                  tol >= kDfResidualTol)));
-    CK(cocg_scalars(S, cv64.tiles, cv64.part, cv64.sysd, cv64.sysi, 4, 1 << kConverged, tol, itol,
-                    maxit, 0, c->stream));
+                                  tol >= kDfResidualTol,
+                                  cont ? c->p2.as<cpx<float>>() : nullptr)));
+    CK(cocg_scalars(S, cv64.tiles, cv64.part, cv64.sysd, cv64.sysi, cont ? 6 : 4,
+                    1 << kConverged, tol, itol, maxit, 0, c->stream));
     int cnt[kNumStatus];
     CKS(counts(c, S, cnt));
     if (cnt[kActive] == 0) break;
-    CKS(cocg_loop<float>(c, cv, maxit));
+    CKS(cocg_loop<float>(c, cv, maxit, cont));
     const int corrected = (1 << kConverged) | (1 << kMaxit) | (1 << kBreakdown);
     CK((accumulate<double, float>(c->nd, S, c->sysi.as<int>(), corrected, round, x, x64, 0,
                                   c->stream)));
     // systems that were final before this round keep status kFinal and are skipped above;
     // systems corrected this round are kConverged again and are re-checked next round.
+    rounds_left = true;
+  }
+  if (rounds_left) {
+    // the rounds are used up: check the last corrections in FP64, so that a system still
+    // above the tolerance is reported (not converged) instead of passing silently
+    int cnt[kNumStatus];
+    CKS(counts(c, S, cnt));
+    if (cnt[kConverged] > 0) {
+      CK(proj_dots<double>(cv64.nl, c->nd, S, x64, cv64.sysi, 1 << kConverged, cv64.cdot,
+                           c->stream));
+      CK((cocg_resid<double, float>(cv64, x64, r64, nullptr, 1 << kConverged, nullptr, nullptr,
+                                    nullptr, c->stream, tol >= kDfResidualTol)));
+      CK(cocg_scalars(S, cv64.tiles, cv64.part, cv64.sysd, cv64.sysi, 7, 1 << kConverged, tol,
+                      itol, maxit, 0, c->stream));
+    }
   }
   CKS(collect_stats(c, S, ss));
   CK((density<double, double>(c->nd, c->ns, nb, c->d64.psi.as<double>(), x64, active,
@@ -1002,6 +1062,8 @@ static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const d
     CK(cudaStreamSynchronize(c->stream));
     if (st) {
       st->solves += ss.solves;
+      st->nonconv_solves += ss.nonconv;
+      st->breakdown_solves += ss.breakdown;
       st->cocg_iters += ss.iters;
       st->refine_rounds += ss.refine_rounds;
       st->max_cocg_iters = std::max(st->max_cocg_iters, ss.max_iters);
@@ -1010,7 +1072,10 @@ static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const d
       CKS(timing_add(c, st, 2, 3, 0));
       CKS(timing_add(c, st, 3, 4, 4));
     }
-    if (ss.nonconv) c->err = "a Sternheimer solve reached stern_maxit";
+    if (ss.nonconv) note_soft(c, RPA_ENOCONV, "a Sternheimer solve reached stern_maxit");
+    if (ss.breakdown)
+      note_soft(c, RPA_EBREAKDOWN,
+                "a COCG solve broke down (p^T A p = 0 or a non-finite residual)");
     int any = 0;
     for (int b = 0; b < nb; ++b) any += act[b];
     // one matrix-vector product per probe-point that ran this step
@@ -1053,6 +1118,7 @@ static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const d
   CK(cudaMemcpyAsync(flags, c->flags_d.p, sizeof(flags), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (flags[2]) return fail(c, RPA_ETIMEOUT, "a bounded tensor-core wait expired");
+  if (flags[0] & 1) note_soft(c, RPA_EBREAKDOWN, "a Lanczos scalar (alpha or beta) is not finite");
   if (out.steps) std::memcpy(out.steps, steps.data(), sizeof(int) * nb);
   if (st) {
     CKS(timing_add(c, st, 5, 6, 5));
@@ -1065,13 +1131,12 @@ static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const d
 // Run count probe-points in waves; d/alpha/beta/steps are host arrays in input order.
 static rpa_status run_probes(rpa_ctx* c, long long count, const long long* probe,
                              const double* omg, double* d, double* alpha, double* beta,
-                             int* steps, rpa_stats* st, bool* nonconv) {
+                             int* steps, rpa_stats* st) {
   if (count == 0) return RPA_OK;
   const int nb_max = choose_batch(c, count);
   CKS(ensure_workspace(c, nb_max));
   const int nl = c->opt.lanczos_max;
   const int bmax = c->opt.lanczos_block;
-  *nonconv = false;
   if (bmax > 1) {
     // blocks: runs of consecutive entries with one frequency and distinct points, at most
     // bmax long; waves hold whole blocks
@@ -1108,7 +1173,6 @@ static rpa_status run_probes(rpa_ctx* c, long long count, const long long* probe
         }
       }
       if (nb > nb_max) CKS(ensure_workspace(c, nb));
-      c->err.clear();
       WaveOut o;
       o.d = d + s0;
       o.alpha = nullptr;  // no scalar tridiagonal in block mode
@@ -1117,21 +1181,18 @@ static rpa_status run_probes(rpa_ctx* c, long long count, const long long* probe
       if (alpha) std::memset(alpha + s0 * nl, 0, sizeof(double) * nb * nl);
       if (beta) std::memset(beta + s0 * nl, 0, sizeof(double) * nb * nl);
       CKS(run_wave(c, nb, probe + s0, omg + s0, o, st, &L));
-      if (!c->err.empty()) *nonconv = true;
       bi = be;
     }
     return RPA_OK;
   }
   for (long long s0 = 0; s0 < count; s0 += nb_max) {
     const int nb = (int)std::min<long long>(nb_max, count - s0);
-    c->err.clear();
     WaveOut o;
     o.d = d + s0;
     o.alpha = alpha ? alpha + s0 * nl : nullptr;
     o.beta = beta ? beta + s0 * nl : nullptr;
     o.steps = steps ? steps + s0 : nullptr;
     CKS(run_wave(c, nb, probe + s0, omg + s0, o, st));
-    if (!c->err.empty()) *nonconv = true;
   }
   return RPA_OK;
 }
@@ -1234,7 +1295,7 @@ rpa_status rpa_default_options(rpa_options* o) {
   o->lanczos_max = 20;
   o->lanczos_rtol = 0.0;
   o->stern_tol = 1e-10;
-  o->stern_maxit = 2000;
+  o->stern_maxit = 20000;
   o->precision = RPA_FP64;
   o->reorth = 1;
   o->stride[0] = o->stride[1] = o->stride[2] = 1;
@@ -1246,6 +1307,8 @@ rpa_status rpa_default_options(rpa_options* o) {
   o->tile = -1;
   o->graphs = 1;
   o->lanczos_block = 1;
+  o->refine_restart = 0;
+  o->debug_expire_waits = 0;
   return RPA_OK;
 }
 
@@ -1516,15 +1579,25 @@ rpa_status rpa_set_options(rpa_ctx* c, const rpa_options* o) {
   if (o->tile == kTileX2) {
     if (o->precision == RPA_FP64 || !x2_tile_fits(c->grid.n[0], c->grid.fd_radius))
       return fail(c, RPA_EINVAL, "two-point tiles need the mixed form and an even nx");
+  } else if (is_band(o->tile)) {
+    if (o->precision == RPA_FP64 ||
+        !band_tile_fits(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, band_rows(o->tile),
+                        c->ngroup))
+      return fail(c, RPA_EINVAL, "band tiles need the mixed form, an even nx <= 64 and a band "
+                                 "height that divides ny");
   } else if (o->tile > 0) {
     const bool ok = o->precision == RPA_FP64
                         ? row_tile_fits<double>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, o->tile)
                         : row_tile_fits<float>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, o->tile);
     if (!ok) return fail(c, RPA_EINVAL, "row-tile height does not fit this grid");
-  } else if (o->tile < -2) {
+  } else if (o->tile < -2) {  // -3 .. -100
     return fail(c, RPA_EINVAL, "bad tile option");
   }
   if (o->graphs != 0 && o->graphs != 1) return fail(c, RPA_EINVAL, "bad graphs option");
+  if (o->refine_restart != 0 && o->refine_restart != 1)
+    return fail(c, RPA_EINVAL, "bad refine_restart option");
+  if (o->debug_expire_waits != 0 && o->debug_expire_waits != 1)
+    return fail(c, RPA_EINVAL, "bad debug_expire_waits option");
   if (o->lanczos_block < 1 || o->lanczos_block > block_max())
     return fail(c, RPA_EINVAL, "lanczos_block out of range");
   if (o->lanczos_block > 1 && (o->lanczos_rtol != 0.0 || !o->reorth))
@@ -1584,10 +1657,10 @@ rpa_status rpa_probe_density(rpa_ctx* c, int count, const long long* probe, cons
   const int nl = c->opt.lanczos_max;
   std::vector<double> dh(count), ah(alpha ? (size_t)count * nl : 0), bh(beta ? (size_t)count * nl : 0);
   std::vector<int> sh(steps ? count : 0);
-  bool nonconv = false;
+  c->soft = RPA_OK;
   rpa_status rs = run_probes(c, count, pr.data(), om.data(), dh.data(),
                              alpha ? ah.data() : nullptr, beta ? bh.data() : nullptr,
-                             steps ? sh.data() : nullptr, st, &nonconv);
+                             steps ? sh.data() : nullptr, st);
   c->prof_stats = nullptr;
   CKS(rs);
   CKS(copy_out(c, d, dh.data(), sizeof(double) * count, where));
@@ -1596,8 +1669,7 @@ rpa_status rpa_probe_density(rpa_ctx* c, int count, const long long* probe, cons
   if (steps) CKS(copy_out(c, steps, sh.data(), sizeof(int) * count, where));
   CK(cudaStreamSynchronize(c->stream));
   if (st) st->seconds_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (nonconv) return fail(c, RPA_ENOCONV, "a Sternheimer solve reached stern_maxit");
-  return RPA_OK;
+  return soft_status(c);
 }
 
 rpa_status rpa_batch_energy(int nsys, rpa_ctx* const* sys, double* ec_out, rpa_stats* stats) {
@@ -1657,9 +1729,9 @@ rpa_status rpa_energy_density(rpa_ctx* c, double* d_coarse, double* d_fine, doub
       pr[k * P + j] = idx[j];
       om[k * P + j] = c->omega[k];
     }
-  bool nonconv = false;
+  c->soft = RPA_OK;
   rpa_status rs = run_probes(c, count, pr.data(), om.data(), dh.data(), nullptr, nullptr,
-                             nullptr, st, &nonconv);
+                             nullptr, st);
   c->prof_stats = nullptr;
   CKS(rs);
   auto t1 = std::chrono::steady_clock::now();
@@ -1678,8 +1750,7 @@ rpa_status rpa_energy_density(rpa_ctx* c, double* d_coarse, double* d_fine, doub
     st->seconds_phase[6] += std::chrono::duration<double>(t2 - t1).count();
     st->seconds_total = std::chrono::duration<double>(t2 - t0).count();
   }
-  if (nonconv) return fail(c, RPA_ENOCONV, "a Sternheimer solve reached stern_maxit");
-  return RPA_OK;
+  return soft_status(c);
 }
 
 rpa_status rpa_apply_h(rpa_ctx* c, int count, const double* x, const double* sigma, double* y,
@@ -1758,7 +1829,7 @@ rpa_status rpa_chi0(rpa_ctx* c, int count, const double* omega, const double* u,
     std::memcpy(om.data(), omega, sizeof(double) * count);
   for (int i = 0; i < count; ++i)
     if (!(om[i] > 0.0)) return fail(c, RPA_EINVAL, "omega must be positive");
-  bool nonconv = false;
+  c->soft = RPA_OK;
   for (int s0 = 0; s0 < count; s0 += nb_max) {
     const int nb = std::min(nb_max, count - s0);
     std::vector<int> ones(nb, 1);
@@ -1773,7 +1844,10 @@ rpa_status rpa_chi0(rpa_ctx* c, int count, const double* omega, const double* u,
     } else {
       CKS(solve_fp64(c, nb, c->u64.as<double>(), c->active_d.as<int>(), ss));
     }
-    if (ss.nonconv) nonconv = true;
+    if (ss.nonconv) note_soft(c, RPA_ENOCONV, "a Sternheimer solve reached stern_maxit");
+    if (ss.breakdown)
+      note_soft(c, RPA_EBREAKDOWN,
+                "a COCG solve broke down (p^T A p = 0 or a non-finite residual)");
     CKS(copy_out(c, r + (long long)s0 * c->nd, c->dens64.p, sizeof(double) * nb * c->nd, where));
     if (iters) {
       std::vector<int> si((size_t)nb * c->ns * kSysI);
@@ -1786,8 +1860,7 @@ rpa_status rpa_chi0(rpa_ctx* c, int count, const double* omega, const double* u,
     }
     CK(cudaStreamSynchronize(c->stream));
   }
-  if (nonconv) return fail(c, RPA_ENOCONV, "a Sternheimer solve reached stern_maxit");
-  return RPA_OK;
+  return soft_status(c);
 }
 
 rpa_status rpa_galerkin(rpa_ctx* c, int count, const double* omega, const double* u, double* x0,
@@ -1824,7 +1897,7 @@ rpa_status rpa_galerkin(rpa_ctx* c, int count, const double* omega, const double
                            c->dV, c->gpart.as<double>(), gram_chunks(nd),
                            c->cmat.as<cpx<float>>(), c->x.as<cpx<float>>(),
                            c->flags_d.as<int>() + 2, c->stream,
-                           c->opt.precision == RPA_MIXED_BF16));
+                           c->opt.precision == RPA_MIXED_BF16, c->opt.debug_expire_waits));
       CK(convert_f2d(c->x.as<float>(), xo.as<double>(), 2 * n, c->stream));
     } else {
       CK(galerkin_guess<double>(nd, c->ns, nb, c->d64.psi.as<double>(), c->eps_d.as<double>(),

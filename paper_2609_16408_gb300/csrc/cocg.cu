@@ -219,6 +219,7 @@ __global__ void k_scalars(int nsys, int tiles, int stride, const double* __restr
     sd[kRho + 1] = v[3];
     si[kIters] = 0;
     si[kRestarts] = 0;
+    si[kIterBase] = 0;
     si[kStatus] = (bn == 0.0 || rn <= tol * bn) ? kFinal : kActive;
     if (!isfinite(rn) || !isfinite(bn)) si[kStatus] = kBreakdown;
   } else if (kind == 1) {  // alpha = rho / (p^T A p)
@@ -255,27 +256,47 @@ __global__ void k_scalars(int nsys, int tiles, int stride, const double* __restr
   } else if (kind == 3) {  // true residual of a recursively converged system
     const double rn = sqrt(v[0]);
     sd[kRnormTrue] = rn;
-    if (rn <= sd[kTarget] || si[kRestarts] >= max_restart) {
+    if (rn <= sd[kTarget]) {
       si[kStatus] = kFinal;
+    } else if (si[kRestarts] >= max_restart || !isfinite(rn)) {
+      // the restarts are used up and the true residual still misses the tolerance
+      si[kStatus] = isfinite(rn) ? kMaxit : kBreakdown;
     } else {
       si[kRestarts] += 1;
       sd[kRho] = v[2];
       sd[kRho + 1] = v[3];
       si[kStatus] = (si[kIters] >= maxit) ? kMaxit : kActive;
     }
-  } else if (kind == 4) {  // mixed form: FP64 residual of the current FP64 iterate
+  } else if (kind == 4 || kind == 6) {  // mixed form: FP64 residual of the FP64 iterate
     const double rn = sqrt(v[0]);
     sd[kRnormTrue] = rn;
     if (rn <= tol * sd[kBnorm] || !isfinite(rn)) {
       si[kStatus] = isfinite(rn) ? kFinal : kBreakdown;
     } else {
-      // correction round: solve A d = r in low precision from d = 0
+      // correction round: solve A d = r in low precision from d = 0.  kind 4 restarts the
+      // recurrence (p = r); kind 6 keeps the previous direction and continues it with the
+      // true residual in place of the recursive one: beta = rho_new / rho_k, where rho_k
+      // (still in sysd) belongs to the residual that formed the last direction.  When the
+      // true residual has drifted far above the recursive one (|beta| > 4: the low-precision
+      // recurrence went below what its rounding can resolve), the old direction no longer
+      // fits the new residual and the round restarts instead (beta = 0, p = r).
       sd[kTarget] = fmax(inner_tol * rn, 0.5 * tol * sd[kBnorm]);
+      double br = 0.0, bi = 0.0;
+      if (kind == 6 && si[kIters] > si[kIterBase])
+        cdiv(v[2], v[3], sd[kRho], sd[kRho + 1], br, bi);
+      if (!isfinite(br) || !isfinite(bi) || br * br + bi * bi > 16.0) br = bi = 0.0;
+      sd[kBeta] = br;
+      sd[kBeta + 1] = bi;
       sd[kRho] = v[2];
       sd[kRho + 1] = v[3];
+      si[kIterBase] = si[kIters];
       si[kStatus] = (si[kIters] >= maxit) ? kMaxit : kActive;
       si[kRestarts] += 1;
     }
+  } else if (kind == 7) {  // mixed form, after the last refinement round: final FP64 check
+    const double rn = sqrt(v[0]);
+    sd[kRnormTrue] = rn;
+    si[kStatus] = !isfinite(rn) ? kBreakdown : (rn <= tol * sd[kBnorm] ? kFinal : kMaxit);
   } else if (kind == 5) {  // mixed form init: low-precision round 0 target
     const double rn = sqrt(v[0]), bn = sqrt(v[1]);
     sd[kBnorm] = bn;
@@ -285,6 +306,7 @@ __global__ void k_scalars(int nsys, int tiles, int stride, const double* __restr
     sd[kRho + 1] = v[3];
     si[kIters] = 0;
     si[kRestarts] = 0;
+    si[kIterBase] = 0;
     si[kStatus] = (bn == 0.0 || rn <= inner_tol * bn) ? kConverged : kActive;
     if (!isfinite(rn) || !isfinite(bn)) si[kStatus] = kBreakdown;
   }

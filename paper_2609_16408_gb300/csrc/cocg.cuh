@@ -14,7 +14,8 @@ constexpr int kRho = 0, kAlpha = 2, kBeta = 4, kBnorm = 6, kTarget = 7, kRnorm =
               kRnormTrue = 9;
 // per-system ints
 constexpr int kSysI = 4;
-constexpr int kStatus = 0, kIters = 1, kRestarts = 2;
+constexpr int kStatus = 0, kIters = 1, kRestarts = 2,
+              kIterBase = 3;  // kIters when the current COCG loop started
 // statuses
 constexpr int kActive = 0, kConverged = 1, kFinal = 2, kMaxit = 3, kBreakdown = 4, kIdle = 5;
 constexpr int kNumStatus = 6;
@@ -45,12 +46,19 @@ template <typename T>
 cudaError_t apply_h(const Stencil<T>& st, const T* vloc, const NonlocalDev<T>& nl, long long nd,
                     int count, const cpx<T>* x, const cpx<T>* sigma, cpx<T>* cd, cpx<T>* y,
                     cudaStream_t s);
+// With r_lo: the low-precision copy r_lo = r, x_lo = 0, and p_lo = r_lo (restart) -- or, with
+// p_keep, the direction of the previous loop is kept for a continued recurrence: it is
+// copied from p_keep into p_lo for systems whose last loop ran an odd number of iterations
+// (their latest direction is in the other buffer of the pair), and p_lo = r_lo only for
+// systems that did not iterate.
 template <typename T, typename TL>
 cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
                        cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s,
-                       bool use_df = false);
+                       bool use_df = false, const cpx<TL>* p_keep = nullptr);
 // Per-system scalar step (kind: 0 init, 1 alpha, 2 beta/convergence, 3 true-residual
-// recheck, 4 FP64 refinement check, 5 mixed-form init).  `tiles` partial sums per system are
+// recheck, 4 FP64 refinement check (restart), 5 mixed-form init, 6 FP64 refinement check
+// continuing the recurrence: beta = rho(new true residual) / rho(last recursive step),
+// 7 final FP64 check after the last refinement round: final, or not converged).  `tiles` partial sums per system are
 // added; `stride` (default tiles) is the per-system stride of the partial-sum buffer.
 // With list != null, nsys is the length of the list and the step runs for listed systems.
 cudaError_t cocg_scalars(int nsys, int tiles, const double* part, double* sysd, int* sysi,
@@ -81,11 +89,13 @@ cudaError_t galerkin_guess(long long nd, int ns, int nb, const T* psi, const dou
                            const double* omega, const T* u, const int* probe_active, double dV,
                            double* gpart, int nchunk, cpx<T>* cmat, cpx<T>* x0, cudaStream_t s);
 // The same projection on the tensor cores (umma.cu, tcgen05 kind::tf32, 3-pass tf32 split):
-// FP32 operands, FP32 results; err receives 1 if a bounded tensor-core wait expired.
+// FP32 operands, FP32 results; err receives 1 if a bounded tensor-core wait expired
+// (test_expire: make the first wait of every block expire, see umma.cu).
 cudaError_t galerkin_guess_tc(long long nd, int ns, int nb, const float* psi, const double* eps,
                               const double* omega, const float* u, const int* probe_active,
                               double dV, double* gpart, int nchunk, cpx<float>* cmat,
-                              cpx<float>* x0, int* err, cudaStream_t s, bool bf16 = false);
+                              cpx<float>* x0, int* err, cudaStream_t s, bool bf16 = false,
+                              int test_expire = 0);
 // Mode products along one axis of a batch of 3-D arrays: out[..a..] = sum_i Mt[i][a] in[..i..]
 // (Mt is nin x nout, row-major).  dims_in = (nx, ny, nz) of the input; batch strides in_bs and
 // out_bs.  Optional elementwise scale of the output (same layout as the output).

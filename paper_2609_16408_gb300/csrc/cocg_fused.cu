@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
     }
   };
   if (z0 < z1) prefetch(z0);
-  T acc_re = 0, acc_im = 0;
+  using A = dacc_t<T>;
+  A acc_re = 0, acc_im = 0;
   const T c0 = st.c0;
   for (int z = z0; z < z1; ++z) {
     const int bo = ((z - z0) & 1) * PLN;
@@ -187,14 +188,15 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
       }
       w[q] = a;
       pn[q] = c;
-      acc_re += c.re * a.re - c.im * a.im;
-      acc_im += c.re * a.im + c.im * a.re;
+      acc_re += (A)c.re * a.re - (A)c.im * a.im;
+      acc_im += (A)c.re * a.im + (A)c.im * a.re;
     }
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) zq[i] = zq[i + 1];
   }
-  T acc2[2] = {acc_re, acc_im};
-  block_sum_t<T, 2>(acc2, sh);
+  A acc2[2] = {acc_re, acc_im};
+  __shared__ A sha[8 * 2];
+  block_sum_t<A, 2>(acc2, sha);
   if (threadIdx.x == 0) {
     const int pid = blockIdx.x + gridDim.x * blockIdx.z;
     double* pp = cv.part + ((long long)s * cv.tiles + pid) * 4;
@@ -218,7 +220,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_update_dots(Coc
   const double* sd = cv.sysd + (long long)s * kSysD;
   const cpx<T> al = mk<T>((T)sd[kAlpha], (T)sd[kAlpha + 1]);
   const bool nl = cv.nl.ngroup > 0;
-  T a0 = 0, a1 = 0, a2 = 0;
+  using A = dacc_t<T>;
+  A a0 = 0, a1 = 0, a2 = 0;
   const long long t0 = (long long)blockIdx.x * kTile;
   const long long t1 = min(t0 + kTile, nd);
   const cpx<T>* __restrict__ pp_ = fb.p_out + (long long)s * nd;
@@ -245,12 +248,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_update_dots(Coc
       const cpx<T> rv = csub(rv0[u], cmul(al, wv[u]));
       rr_[p] = rv;
       if (nl) sr[p - t0] = rv;
-      a0 += rv.re * rv.re + rv.im * rv.im;
-      a1 += rv.re * rv.re - rv.im * rv.im;
-      a2 += (T)2 * rv.re * rv.im;
+      a0 += (A)rv.re * rv.re + (A)rv.im * rv.im;
+      a1 += (A)rv.re * rv.re - (A)rv.im * rv.im;
+      a2 += (A)2 * rv.re * rv.im;
     }
   }
-  T acc[3] = {a0, a1, a2};
+  A acc[3] = {a0, a1, a2};
   if (nl) {
     __syncthreads();
     cpx<T>* cr = fb.cr + (long long)s * cv.nl.ngroup * kProjChunk;
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_update_dots(Coc
       }
     }
   }
-  block_sum_t<T, 3>(acc, reinterpret_cast<T*>(sh));
+  block_sum_t<A, 3>(acc, reinterpret_cast<A*>(sh));
   if (threadIdx.x == 0) {
     double* pp = cv.part + ((long long)s * cv.tiles + blockIdx.x) * 4;
     pp[0] = (double)acc[0];
@@ -357,6 +360,15 @@ static void launch_dirmatvec(const CocgView<T>& cv, const FusedBufs<T>& fb, cuda
 
 template <typename T>
 cudaError_t launch_dirmatvec_only(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s) {
+  if (is_band(fb.row_ty)) {
+    if constexpr (sizeof(T) == 4) {
+      cudaError_t e = launch_dirmatvec_band(cv, fb, s);
+      note_launch();
+      return e;
+    } else {
+      return cudaErrorInvalidValue;  // FP32 only
+    }
+  }
   if (fb.row_ty == kTileX2) {
     if constexpr (sizeof(T) == 4) {
       cudaError_t e = launch_dirmatvec_x2(cv, fb, s);
@@ -421,9 +433,10 @@ cudaError_t fused_iteration(const CocgView<T>& cv, const FusedBufs<T>& fb, doubl
 }
 
 template <typename T>
-cudaError_t fused_prepare(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s) {
+cudaError_t fused_prepare(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s,
+                          int init) {
   if (cv.nl.ngroup == 0) return cudaSuccess;
-  k_proj_next<T><<<(cv.nsys + 3) / 4, 128, 0, s>>>(cv.nsys, cv.nl.ngroup, cv.sysd, cv.sysi, 1,
+  k_proj_next<T><<<(cv.nsys + 3) / 4, 128, 0, s>>>(cv.nsys, cv.nl.ngroup, cv.sysd, cv.sysi, init,
                                                    fb.cp, fb.cr, nullptr);
   note_launch();
   return cudaGetLastError();
@@ -434,8 +447,8 @@ template cudaError_t fused_iteration<double>(const CocgView<double>&, const Fuse
 template cudaError_t fused_iteration<float>(const CocgView<float>&, const FusedBufs<float>&,
                                             double, int, cudaStream_t, cudaEvent_t*);
 template cudaError_t fused_prepare<double>(const CocgView<double>&, const FusedBufs<double>&,
-                                           cudaStream_t);
+                                           cudaStream_t, int);
 template cudaError_t fused_prepare<float>(const CocgView<float>&, const FusedBufs<float>&,
-                                          cudaStream_t);
+                                          cudaStream_t, int);
 
 }  // namespace rpa

@@ -17,10 +17,24 @@ struct FusedBufs {
   int nact;                // launched systems: the first nact entries of CocgView::list
   int cd_in_smem;          // stage the projector coefficients of a system in shared memory
   int row_ty;              // 0: 32 x 8 column tiles; > 0: row tiles of this height (nx <= 64);
-                           // kTileX2: 64 x 8 tiles, two x points per thread (FP32, nx even)
+                           // kTileX2: 64 x 8 tiles, two x points per thread (FP32, nx even);
+                           // band_code(h): bands of h full rows, two points per thread
+  int band_ty;             // rows of a band (band tiling only)
 };
 
 constexpr int kTileX2 = -2;
+// tiling codes of the band kernel: -100 - h for bands of h rows
+constexpr int kTileBandBase = -100;
+inline int band_code(int ty) { return kTileBandBase - ty; }
+inline bool is_band(int code) { return code < kTileBandBase; }
+inline int band_rows(int code) { return kTileBandBase - code; }
+// band kernel (FP32, nx even and <= 64, h | ny): whether bands of ty rows fit, the heights
+// worth timing, its one-time function attributes (call before a stream capture), the launch
+bool band_tile_fits(int nx, int ny, int R, int ty, int ngroup);
+int band_candidates(int nx, int ny, int R, int ngroup, int* out, int maxn);
+cudaError_t launch_dirmatvec_band_prepare();
+cudaError_t launch_dirmatvec_band(const CocgView<float>& cv, const FusedBufs<float>& fb,
+                                  cudaStream_t s);
 bool x2_tile_fits(int nx, int R);
 int x2_tiles_xy(int nx, int ny);
 cudaError_t launch_dirmatvec_x2(const CocgView<float>& cv, const FusedBufs<float>& fb,
@@ -45,8 +59,10 @@ cudaError_t launch_dirmatvec_only(const CocgView<T>& cv, const FusedBufs<T>& fb,
 template <typename T>
 cudaError_t fused_iteration(const CocgView<T>& cv, const FusedBufs<T>& fb, double tol, int maxit,
                             cudaStream_t s, cudaEvent_t* ev = nullptr);
-// cp = cr, cr = 0 for every active system (start of a solve or restart)
+// For every active system: cp = cr (start of a solve or restart, init = 1) or
+// cp = cr + beta cp (a recurrence continued from the kept direction, init = 0); cr = 0.
 template <typename T>
-cudaError_t fused_prepare(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s);
+cudaError_t fused_prepare(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s,
+                          int init = 1);
 
 }  // namespace rpa

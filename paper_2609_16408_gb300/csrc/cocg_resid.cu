@@ -76,11 +76,18 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
     k_resid_fused(CocgView<T> cv, const cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
                   cpx<T>* __restrict__ pdir, int mask, cpx<TL>* __restrict__ r_lo,
                   cpx<TL>* __restrict__ p_lo, cpx<TL>* __restrict__ x_lo, int zchunk,
-                  DfCoef dc) {
+                  DfCoef dc, const cpx<TL>* __restrict__ p_keep) {
   using V = typename std::conditional<DF, cdf, cpx<T>>::type;  // stored neighbour values
   const int s = blockIdx.y;
   const int st_s = cv.sysi[(long long)s * kSysI + kStatus];
   if (!((mask >> st_s) & 1)) return;
+  // direction of the low-precision recurrence: 0 restart (p_lo = r_lo), 1 keep p_lo,
+  // 2 copy the kept direction from p_keep (see cocg_resid)
+  int pmode = 0;
+  if (p_keep) {
+    const int ran = cv.sysi[(long long)s * kSysI + kIters] - cv.sysi[(long long)s * kSysI + kIterBase];
+    pmode = ran <= 0 ? 0 : ((ran & 1) ? 2 : 1);
+  }
   constexpr int EXN = kRTX + 2 * R, EYN = kRTY + 2 * R;
   constexpr int PLN = EXN * EYN;
   constexpr int NHALO = PLN - kRTX * kRTY;
@@ -245,7 +252,10 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
       if (r_lo) {
         const cpx<TL> rl = mk<TL>((TL)rv.re, (TL)rv.im);
         r_lo[sbase + q] = rl;
-        p_lo[sbase + q] = rl;
+        if (pmode == 0)
+          p_lo[sbase + q] = rl;
+        else if (pmode == 2)
+          p_lo[sbase + q] = p_keep[sbase + q];
         x_lo[sbase + q] = mk<TL>((TL)0, (TL)0);
       }
       a0 += rv.re * rv.re + rv.im * rv.im;
@@ -268,7 +278,8 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
 
 template <typename T, typename TL, int R>
 void launch_r(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
-              cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, bool use_df, cudaStream_t s) {
+              cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, bool use_df,
+              const cpx<TL>* p_keep, cudaStream_t s) {
   constexpr size_t kPlanes = 2 * sizeof(cpx<T>) * (kRTX + 2 * R) * (kRTY + 2 * R);
   size_t cdb = sizeof(cpx<T>) * cv.nl.ngroup * kProjChunk;
   if (cdb + kPlanes + 1024 > 48 * 1024) cdb = 0;
@@ -292,19 +303,19 @@ void launch_r(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, i
     if (use_df) {
       if (cdb)
         k_resid_fused<T, TL, R, true, true><<<grid, kRTX * kRTY, cdb, s>>>(
-            cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc);
+            cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc, p_keep);
       else
         k_resid_fused<T, TL, R, false, true><<<grid, kRTX * kRTY, 0, s>>>(
-            cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc);
+            cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc, p_keep);
       return;
     }
   }
   if (cdb)
-    k_resid_fused<T, TL, R, true, false><<<grid, kRTX * kRTY, cdb, s>>>(cv, x, r, pdir, mask, r_lo,
-                                                                          p_lo, x_lo, zchunk, dc);
+    k_resid_fused<T, TL, R, true, false><<<grid, kRTX * kRTY, cdb, s>>>(
+        cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc, p_keep);
   else
-    k_resid_fused<T, TL, R, false, false><<<grid, kRTX * kRTY, 0, s>>>(cv, x, r, pdir, mask, r_lo,
-                                                                         p_lo, x_lo, zchunk, dc);
+    k_resid_fused<T, TL, R, false, false><<<grid, kRTX * kRTY, 0, s>>>(
+        cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc, p_keep);
 }
 
 }  // namespace
@@ -312,21 +323,22 @@ void launch_r(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, i
 template <typename T, typename TL>
 cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
                        cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s,
-                       bool use_df) {
+                       bool use_df, const cpx<TL>* p_keep) {
+  if (p_keep && !r_lo) return cudaErrorInvalidValue;
   const int nx = cv.st.nx, ny = cv.st.ny, nz = cv.st.nz;
   const int zchunk = nz <= 64 ? nz : 32;
   const long long used = (long long)((nx + kRTX - 1) / kRTX) * ((ny + kRTY - 1) / kRTY) *
                          ((nz + zchunk - 1) / zchunk);
   if (used > cv.tiles) return cudaErrorInvalidValue;  // partial buffer too small
   switch (cv.st.R) {
-    case 1: launch_r<T, TL, 1>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
-    case 2: launch_r<T, TL, 2>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
-    case 3: launch_r<T, TL, 3>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
-    case 4: launch_r<T, TL, 4>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
-    case 5: launch_r<T, TL, 5>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
-    case 6: launch_r<T, TL, 6>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
-    case 7: launch_r<T, TL, 7>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
-    default: launch_r<T, TL, 8>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, s); break;
+    case 1: launch_r<T, TL, 1>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
+    case 2: launch_r<T, TL, 2>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
+    case 3: launch_r<T, TL, 3>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
+    case 4: launch_r<T, TL, 4>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
+    case 5: launch_r<T, TL, 5>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
+    case 6: launch_r<T, TL, 6>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
+    case 7: launch_r<T, TL, 7>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
+    default: launch_r<T, TL, 8>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
   }
   note_launch();
   return cudaGetLastError();
@@ -334,12 +346,15 @@ cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>
 
 template cudaError_t cocg_resid<double, double>(const CocgView<double>&, const cpx<double>*,
                                                 cpx<double>*, cpx<double>*, int, cpx<double>*,
-                                                cpx<double>*, cpx<double>*, cudaStream_t, bool);
+                                                cpx<double>*, cpx<double>*, cudaStream_t, bool,
+                                                const cpx<double>*);
 template cudaError_t cocg_resid<double, float>(const CocgView<double>&, const cpx<double>*,
                                                cpx<double>*, cpx<double>*, int, cpx<float>*,
-                                               cpx<float>*, cpx<float>*, cudaStream_t, bool);
+                                               cpx<float>*, cpx<float>*, cudaStream_t, bool,
+                                               const cpx<float>*);
 template cudaError_t cocg_resid<float, float>(const CocgView<float>&, const cpx<float>*,
                                               cpx<float>*, cpx<float>*, int, cpx<float>*,
-                                              cpx<float>*, cpx<float>*, cudaStream_t, bool);
+                                              cpx<float>*, cpx<float>*, cudaStream_t, bool,
+                                               const cpx<float>*);
 
 }  // namespace rpa

@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(row_max_threads<T>())
     }
   };
   if (z0 < z1) prefetch(z0);
-  T acc_re = 0, acc_im = 0;
+  using A = dacc_t<T>;
+  A acc_re = 0, acc_im = 0;
   const T c0 = st.c0;
   for (int z = z0; z < z1; ++z) {
     const int bo = ((z - z0) & 1) * PLN;
@@ -201,14 +202,15 @@ __global__ void __launch_bounds__(row_max_threads<T>())
       }
       w[q] = a;
       pn[q] = c;
-      acc_re += c.re * a.re - c.im * a.im;
-      acc_im += c.re * a.im + c.im * a.re;
+      acc_re += (A)c.re * a.re - (A)c.im * a.im;
+      acc_im += (A)c.re * a.im + (A)c.im * a.re;
     }
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) zq[i] = zq[i + 1];
   }
-  T acc2[2] = {acc_re, acc_im};
-  block_sum_t<T, 2>(acc2, sh);
+  A acc2[2] = {acc_re, acc_im};
+  __shared__ A sha[32 * 2];
+  block_sum_t<A, 2>(acc2, sha);
   if (threadIdx.x == 0) {
     const int pid = blockIdx.x + gridDim.x * blockIdx.z;
     double* pp = cv.part + ((long long)s * cv.tiles + pid) * 4;

@@ -182,7 +182,8 @@ __global__ void __launch_bounds__(kX2Threads, 2)
     return a;
   };
   if (z0 < z1) prefetch(z0);
-  T acc_re = 0, acc_im = 0;
+  using A = dacc_t<T>;
+  A acc_re = 0, acc_im = 0;
   const T c0 = st.c0;
   for (int z = z0; z < z1; ++z) {
     const int bo = ((z - z0) & 1) * PLN;
@@ -227,8 +228,8 @@ __global__ void __launch_bounds__(kX2Threads, 2)
       a1 = proj(a1, e1, e2);
       st4(w + q, a0, a1);
       st4(pn + q, c, d);
-      acc_re += c.re * a0.re - c.im * a0.im + d.re * a1.re - d.im * a1.im;
-      acc_im += c.re * a0.im + c.im * a0.re + d.re * a1.im + d.im * a1.re;
+      acc_re += (A)c.re * a0.re - (A)c.im * a0.im + (A)d.re * a1.re - (A)d.im * a1.im;
+      acc_im += (A)c.re * a0.im + (A)c.im * a0.re + (A)d.re * a1.im + (A)d.im * a1.re;
     }
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) {
@@ -236,8 +237,9 @@ __global__ void __launch_bounds__(kX2Threads, 2)
       zb[i] = zb[i + 1];
     }
   }
-  T acc2[2] = {acc_re, acc_im};
-  block_sum_t<T, 2>(acc2, sh);
+  A acc2[2] = {acc_re, acc_im};
+  __shared__ A sha[8 * 2];
+  block_sum_t<A, 2>(acc2, sha);
   if (threadIdx.x == 0) {
     const int pid = blockIdx.x + gridDim.x * blockIdx.z;
     double* pp = cv.part + ((long long)s * cv.tiles + pid) * 4;

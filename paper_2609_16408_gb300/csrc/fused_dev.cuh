@@ -2,7 +2,19 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#ifndef RPA_DOT_F64
+#define RPA_DOT_F64 0
+#endif
+
 namespace rpa {
+
+// Accumulator type of the COCG dot products (p^T w, r^T r, ||r||^2) inside the FP32 kernels:
+// the working precision by default; FP64 (exact products of the FP32 values, FP64 sums) when
+// built with RPA_DOT_F64=1.
+template <typename T>
+using dacc_t = typename std::conditional<RPA_DOT_F64 != 0, double, T>::type;
 
 // periodic wrap (bc 0) of a grid index, or -1 outside a Dirichlet axis
 static __device__ __forceinline__ int wrap_or_neg(int j, int n, int bc) {
