@@ -109,14 +109,16 @@ def test_chi0_mixed(name):
 
 @pytest.mark.parametrize("name,tile", [("per", 0), ("per", 1), ("per", 4), ("per", 11),
                                        ("dir", 3), ("dir", 10), ("mix", 2), ("mix", 9),
-                                       ("per", -2), ("mix", -2)])
+                                       ("per", -2), ("mix", -2), ("per", -111), ("mix", -109)])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_chi0_tilings(name, tile, prec):
     """Every H-apply tiling (32 x 8 column tiles, 64 x 8 two-point tiles, full-row tiles of
-    several heights, ragged last tiles, halos larger than the tile, periodic wrap inside a
-    tile) gives the oracle's chi0 u."""
-    if tile == -2 and prec == "fp64":
-        pytest.skip("two-point tiles are an FP32 kernel")
+    several heights, bands of full rows fed by asynchronous copies (-100 - h), ragged last
+    tiles, halos larger than the tile, periodic wrap inside a tile, an x axis shorter than
+    twice the padding so that edge pairs wrap to both sides, zero-filled Dirichlet halo rows)
+    gives the oracle's chi0 u."""
+    if tile in (-2, -111, -109) and prec == "fp64":
+        pytest.skip("two-point and band tiles are FP32 kernels")
     s = sysfix(name)
     tol = 1e-12 if prec == "fp64" else 1e-10
     c, _, _ = ctx_for(s, precision=prec, stern_tol=tol, refine=4, stern_maxit=5000, tile=tile)
@@ -141,8 +143,13 @@ def test_tile_option_checked():
         R.rpa_set_options(c.ctx, tile=-3)
     with pytest.raises(RuntimeError):
         R.rpa_set_options(c.ctx, precision="fp64", tile=-2)  # FP32 kernel only
+    with pytest.raises(RuntimeError):
+        R.rpa_set_options(c.ctx, precision="fp64", tile=-111)  # FP32 kernel only
+    with pytest.raises(RuntimeError):
+        R.rpa_set_options(c.ctx, precision="mixed", tile=-105)  # 5 rows do not divide 11
     R.rpa_set_options(c.ctx, precision="mixed", tile=11)
     R.rpa_set_options(c.ctx, precision="mixed", tile=-2)
+    R.rpa_set_options(c.ctx, precision="mixed", tile=-111)
     d = sysfix("dir")  # nx = 11: pairs would straddle rows
     cd, _, _ = ctx_for(d, precision="mixed")
     with pytest.raises(RuntimeError):
@@ -366,15 +373,45 @@ def test_device_pointers_round_trip():
     assert np.allclose(out["d"].cpu().numpy(), host["d"], rtol=0, atol=1e-14)
 
 
+def _tf32x3_x0_bound(s, omega, u, lam=8.0):
+    """Element-wise bound on |x0_mixed - x0| (real and imaginary parts) for the TF32x3
+    projection of the mixed form, from its steps:
+      * operands: psi and u rounded to FP32 (relative u32 = 2^-24 each), b = fl32(psi_n u32)
+        (one more u32);
+      * each FP32 product a*b formed as hi*hi + hi*lo + lo*hi of tf32 parts rounded to nearest
+        (hi: 2^-11 relative, lo: 2^-11 of the remainder): the dropped lo*lo and the rounding
+        of the two lo parts leave at most 3 * 2^-22 |a||b|;
+      * the split products (3 per element) accumulated in FP32 in the tensor memory over a
+        chunk of K points (G) or the N_s states (x0): with rounding to nearest, the error of
+        a sum of n terms stays below lam sqrt(n) u32 sum|terms| except with probability about
+        2 n exp(-lam^2 / 2) (Higham and Mary's probabilistic bound; lam = 8);
+      * chunk partial sums added and C = -dV G / (eps_k - eps_n - i w) formed in FP64, then
+        C rounded to FP32 (u32 per component).
+    Propagation: the G error is amplified by dV / |eps_k - eps_n - i w| into C and carried
+    into x0 through |psi_k|."""
+    u32 = 2.0 ** -24
+    split = 3.0 * 2.0 ** -22
+    nd, ns = s.N_d, s.ns
+    nchunk = min(256, max(1, (nd + 4095) // 4096))
+    chunk = (nd + nchunk - 1) // nchunk
+    psi, eps = s.psi, s.eps
+    absum = np.abs(psi) @ (np.abs(psi) * np.abs(u)).T            # sum_r |psi_k||psi_n u|
+    eG = absum * (4 * u32 + split + lam * np.sqrt(3.0 * chunk) * u32)
+    d = eps[:, None] - eps[None, :] - 1j * omega
+    C = -s.dV * (psi @ (psi * u).T) / d
+    dC = s.dV * eG / np.abs(d)
+    rel2 = 2 * u32 + split + lam * np.sqrt(3.0 * ns) * u32       # second GEMM over K = N_s
+    ap = np.abs(psi).T                                             # N_d x N_s
+    bre = ap @ (dC + rel2 * np.abs(C.real))
+    bim = ap @ (dC + rel2 * np.abs(C.imag))
+    return bre.T, bim.T
+
+
 @pytest.mark.parametrize("name", ["per", "dir"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_galerkin_projection(name, prec):
-    """Occupied-space projection GEMMs (tcgen05 tf32 x3 in the mixed form) vs the oracle.
-
-    Mixed tolerance: psi and u are FP32 (6e-8), the tensor cores accumulate in FP32 over
-    chunks of up to 4096 points (~sqrt(4096) x 6e-8 = 4e-6 of the summed magnitudes), and
-    C = G / (eps_k - eps_n - i w) amplifies absolute errors by up to 1/w (50 at w = 0.02)
-    relative to max|x0|: 5e-5 of max|x0|."""
+    """Occupied-space projection GEMMs vs the oracle: FP64 SIMT kernels to 1e-12 of max|x0|;
+    the mixed form (tcgen05 TF32x3) element by element within _tf32x3_x0_bound."""
     s = sysfix(name)
     c, _, _ = ctx_for(s, precision=prec)
     rng = np.random.default_rng(8)
@@ -383,8 +420,12 @@ def test_galerkin_projection(name, prec):
     x0 = R.rpa_galerkin(c.ctx, oms, u, s.ns)
     for i in range(3):
         ref = oracle.galerkin(s, oms[i], u[i])
-        tol = 1e-12 if prec == "fp64" else 5e-5
-        assert np.max(np.abs(x0[i] - ref)) <= tol * np.max(np.abs(ref))
+        if prec == "fp64":
+            assert np.max(np.abs(x0[i] - ref)) <= 1e-12 * np.max(np.abs(ref))
+        else:
+            bre, bim = _tf32x3_x0_bound(s, oms[i], u[i])
+            assert np.all(np.abs(x0[i].real - ref.real) <= bre)
+            assert np.all(np.abs(x0[i].imag - ref.imag) <= bim)
 
 
 def _bf16_x0_bound(s, omega, u):
@@ -456,7 +497,8 @@ def test_chi0_mixed_bf16(name):
 
 
 def test_galerkin_projection_si8_tiles():
-    """Full-size Si8 cell (26^3 points, 16 states): several 128-point tiles, ragged tail."""
+    """Full-size Si8 cell (26^3 points, 16 states): several 128-point tiles, ragged tail,
+    five Gram chunks; element by element within _tf32x3_x0_bound."""
     import synth
     s = synth.named_system("si8")
     c, _, _ = ctx_for(s, precision="mixed")
@@ -465,7 +507,9 @@ def test_galerkin_projection_si8_tiles():
     x0 = R.rpa_galerkin(c.ctx, np.array([0.0132, 2.53]), u, s.ns)
     for i, om in enumerate([0.0132, 2.53]):
         ref = oracle.galerkin(s, om, u[i])
-        assert np.max(np.abs(x0[i] - ref)) <= 1e-4 * np.max(np.abs(ref))
+        bre, bim = _tf32x3_x0_bound(s, om, u[i])
+        assert np.all(np.abs(x0[i].real - ref.real) <= bre)
+        assert np.all(np.abs(x0[i].imag - ref.imag) <= bim)
 
 
 def test_batch_energy_uneven_systems():
