@@ -26,17 +26,21 @@ def probe_point_shard(P: int, nw: int, rank: int, world: int):
 def gather_coarse(d_local, P: int, nw: int, rank: int, world: int, group=None):
     """All-gather the per-rank d values into the full (nw, P) array on every rank.
 
-    d_local: 1-D torch tensor (this rank's shard, in shard order)."""
+    d_local: 1-D torch tensor (this rank's shard, in shard order).  With a backend that
+    cannot exchange device tensors (gloo) the exchange goes through host memory; the result
+    lives where d_local lives."""
     import torch
     import torch.distributed as dist
     counts = [len(probe_point_shard(P, nw, r, world)[0]) for r in range(world)]
     mx = max(counts)
-    buf = torch.zeros(mx, dtype=d_local.dtype, device=d_local.device)
-    buf[: d_local.numel()] = d_local
+    via_host = d_local.is_cuda and dist.get_backend(group) != "nccl"
+    dev = torch.device("cpu") if via_host else d_local.device
+    buf = torch.zeros(mx, dtype=d_local.dtype, device=dev)
+    buf[: d_local.numel()] = d_local.to(dev)
     outs = [torch.zeros_like(buf) for _ in range(world)]
     dist.all_gather(outs, buf, group=group)
     full = torch.cat([o[:c] for o, c in zip(outs, counts)])
-    return full.reshape(nw, P)
+    return full.reshape(nw, P).to(d_local.device)
 
 
 def energy_density_sharded(ctx, P: int, nw: int, nd: int, rank: int, world: int, device,
