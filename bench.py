@@ -147,13 +147,14 @@ def run_reference(args, wl):
     probes = oracle.coarse_probes(s.n, wl["stride"], s.bc)
     cores = os.cpu_count()
     osys = oracle.OracleSystem(s)
-    # Bounded sample: one matrix-vector product (N_s Sternheimer solves) of one probe-point
-    # per step; a probe-point costs N_l such products, so probe-pts/s = 1 / (N_l * t_step).
+    # Bounded sample: one matrix-vector product (N_s Sternheimer solves) of one seeded coarse
+    # point per step, the frequencies taken in turn so that K steps cover all of them
+    # evenly; a probe-point costs N_l such products, so probe-pts/s = 1 / (N_l * t_step).
     times = []
     rng = np.random.default_rng(7)
     for it in range(args.warmup + args.steps):
         j = int(probes[rng.integers(P)])
-        k = int(rng.integers(wl["nw"]))
+        k = it % wl["nw"]
         t0 = time.perf_counter()
         oracle.lanczos(osys, np.array([j]), np.array([om[k]]), 1, tol=wl["tol"], maxit=20000,
                        nthreads=cores)
@@ -163,8 +164,8 @@ def run_reference(args, wl):
     tstep = float(np.mean(times))
     value = 1.0 / (wl["nl"] * tstep)
     sample = (f"per step: 1 Lanczos matrix-vector product ({s.ns} Sternheimer solves, tol "
-              f"{wl['tol']}) of 1 seeded probe-point of the {wl['system']} workload; "
-              f"probe-pts/s = 1/(N_l={wl['nl']} x step time)")
+              f"{wl['tol']}) of 1 seeded coarse point of the {wl['system']} workload, step i at "
+              f"frequency i mod {wl['nw']}; probe-pts/s = 1/(N_l={wl['nl']} x mean step time)")
     line = dict(metric="probe-points/s", value=value, unit="probe-pts/s", n_gpus=args.gpus,
                 steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * tstep,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
@@ -180,21 +181,54 @@ def run_reference(args, wl):
 # ------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------
-def cpu_baseline(s, wl, om, probes):
-    """Oracle on the host cores, bounded sample: one Lanczos matrix-vector product."""
+def oracle_leg(s, wl, om, pidx, seed=11):
+    """The oracle on the host cores, bounded sample: one Lanczos matrix-vector product (N_s
+    Sternheimer solves at the workload's tolerance) for one seeded coarse point at every
+    frequency.  Gives the CPU baseline (probe-pts/s = 1 / (N_l x mean time of a product)) and
+    reference values d = [f(T_1)]_11 for the same (point, frequency) pairs."""
     import oracle
     cores = os.cpu_count()
-    j = int(probes[len(probes) // 3])
-    k = wl["nw"] // 2
-    t0 = time.perf_counter()
-    oracle.lanczos(s, np.array([j]), np.array([om[k]]), 1, tol=wl["tol"], maxit=20000,
-                   nthreads=cores)
-    dt = time.perf_counter() - t0
-    return dict(value=1.0 / (wl["nl"] * dt), unit="probe-pts/s", cores=cores, kind="oracle",
-                per_core=1.0 / (wl["nl"] * dt * cores),
-                sample=(f"1 Lanczos matrix-vector product ({s.ns} Sternheimer solves, tol "
-                        f"{wl['tol']}, omega={om[k]:.4g}) of 1 probe-point; probe-pts/s = "
-                        f"1/(N_l x {dt:.1f} s)"))
+    rng = np.random.default_rng(seed)
+    sel = rng.choice(len(pidx), size=wl["nw"], replace=False)
+    probes = np.asarray(pidx[sel], dtype=np.int64)
+    osys = oracle.OracleSystem(s)
+    times, d = [], []
+    for k in range(wl["nw"]):
+        t0 = time.perf_counter()
+        r = oracle.lanczos(osys, probes[k:k + 1], np.array([om[k]]), 1, tol=wl["tol"],
+                           maxit=20000, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+        d.append(float(r["d"][0]))
+    tm = float(np.mean(times))
+    cpu = dict(value=1.0 / (wl["nl"] * tm), unit="probe-pts/s", cores=cores, kind="oracle",
+               per_core=1.0 / (wl["nl"] * tm * cores),
+               sample=(f"1 Lanczos matrix-vector product ({s.ns} Sternheimer solves, tol "
+                       f"{wl['tol']}) for one seeded coarse point at each of the {wl['nw']} "
+                       f"frequencies; probe-pts/s = 1/(N_l x mean product time {tm:.2f} s); "
+                       f"per-frequency times {[round(t, 2) for t in times]} s"))
+    return cpu, probes, np.asarray(d)
+
+
+def oracle_error(R, context, wl, om, w, probes, d_ref, P, nd, natom):
+    """The GPU forms on the oracle's (point, frequency) pairs with one Lanczos step each:
+    max |d_gpu - d_oracle|, its relative size and the E_c error it implies (one point per
+    frequency standing for all P coarse points, weighted, / 2 pi / atoms), in mHa/atom."""
+    out = {}
+    freqs = np.arange(wl["nw"], dtype=np.int32)
+    for form in ("mixed", "fp64"):
+        c = context(form, profile=0, nl=1)
+        r = R.rpa_probe_density(c.ctx, probes, freqs, allow_nonconv=True)
+        dd = np.asarray(r["d"]) - d_ref
+        g3 = nd / P
+        est = float(np.sum(w * P * dd)) * g3 / (2 * np.pi) / natom
+        out[form] = dict(max_abs_dd=float(np.abs(dd).max()),
+                         max_rel_dd=float(np.max(np.abs(dd) / np.abs(d_ref))),
+                         ec_err_mha_per_atom_est=1e3 * abs(est), status=int(r["status"]))
+        c.close()
+    out["sample"] = (f"one seeded coarse point per frequency ({wl['nw']} probe-points), one "
+                     f"Lanczos step, Sternheimer tol {wl['tol']} on both sides; the oracle is "
+                     "the plain CPU FP64 restatement of Algorithm 1")
+    return out
 
 
 def run_ours(args, wl):
@@ -217,29 +251,42 @@ def run_ours(args, wl):
     nd = s.N_d
     nat = wl["natom"]
 
-    def context(prec, profile=1, tile=-1):
+    mixed_form = "mixed_bf16" if args.proj == "bf16" else "mixed"
+
+    def context(prec, profile=1, tile=-1, nl=None):
         c = R.Context(s.n, s.h, s.bc, s.fd_radius, stream=stream.cuda_stream)
         R.rpa_set_potential(c.ctx, s.vloc)
         R.rpa_set_projectors(c.ctx, [(g.idx, g.chi, g.gamma) for g in s.groups])
         R.rpa_set_occupied(c.ctx, s.psi, s.eps)
         R.rpa_set_frequencies(c.ctx, om, w)
-        R.rpa_set_options(c.ctx, lanczos_max=wl["nl"], stern_tol=wl["tol"], stern_maxit=20000,
-                          precision=prec, stride=wl["stride"], interp=wl["interp"],
-                          refine=args.refine, profile=profile, tile=tile, graphs=args.graphs,
-                          inner_tol=args.inner_tol)
+        R.rpa_set_options(c.ctx, lanczos_max=nl or wl["nl"], stern_tol=wl["tol"],
+                          stern_maxit=20000, precision=mixed_form if prec == "mixed" else prec,
+                          stride=wl["stride"], interp=wl["interp"], refine=args.refine,
+                          profile=profile, tile=tile if prec != "fp64" else -1,
+                          graphs=args.graphs, inner_tol=args.inner_tol)
         return c
 
-    mixed_form = "mixed_bf16" if args.proj == "bf16" else "mixed"
-    cm = context(mixed_form, tile=args.tile)
+    cm = context("mixed", tile=args.tile)
     P = R.rpa_num_probes(cm.ctx)
     probe_idx = torch.from_numpy(R.rpa_probe_indices(cm.ctx)).to(dev)
     dco = torch.zeros((wl["nw"], P), dtype=torch.float64, device=dev)
+    statuses = []
+
+    def sample(per_freq, seed):
+        """This rank's probe-points of one step: a seeded global sample of world x per_freq
+        points per frequency (the same on every rank), partitioned into contiguous blocks by
+        the product's sharding rule."""
+        from paper_2609_16408_gb300.shard import probe_point_shard
+        gsel, gfq = sample_probes(P, wl["nw"], per_freq * world, seed)
+        ids, _ = probe_point_shard(len(gsel), 1, rank, world)
+        return gsel[ids], gfq[ids]
 
     def step(c, per_freq, seed, stats_acc=None):
-        sel, fq = sample_probes(P, wl["nw"], per_freq, seed)
+        sel, fq = sample(per_freq, seed)
         pr = probe_idx[torch.from_numpy(sel).to(dev)]
         fqt = torch.from_numpy(fq).to(dev)
         out = R.rpa_probe_density(c.ctx, pr, fqt, allow_nonconv=True)
+        statuses.append(int(out["status"]))
         dco[fqt.long(), torch.from_numpy(sel).to(dev)] = out["d"]
         dfi, ec = R.rpa_interpolate(c.ctx, dco, nd)
         if stats_acc is not None:
@@ -247,7 +294,7 @@ def run_ours(args, wl):
         return out, sel, fq
 
     per = args.probes_per_freq
-    seed0 = 1000 * (rank + 1)
+    seed0 = 1000
     # warm-up
     for i in range(args.warmup):
         with torch.cuda.stream(stream):
@@ -286,10 +333,17 @@ def run_ours(args, wl):
     tile_tail = int(stats[-1].get("tile_rows_tail", 0)) if stats else 0
 
     def tiling(t):
+        if t <= -101:
+            return (f"bands of {-100 - t} full x rows, two x points per thread, 3-stage "
+                    "cp.async pipeline")
+        if t in (-3, -4):
+            return (f"64 x 8 tiles, two x points per thread, z window in a shared-memory ring, "
+                    f"{1 if t == -3 else 2} centre-plane buffer(s)")
         return (f"{t} full x rows per block" if t > 0
                 else ("64 x 8 tiles, two x points per thread" if t == -2 else "32 x 8 column tiles"))
-    hname = ("k_dirmatvec_rows" if tile_rows > 0
-             else ("k_dirmatvec_x2" if tile_rows == -2 else "k_dirmatvec"))
+    hname = ("k_dirmatvec_band" if tile_rows <= -101
+             else "k_dirmatvec_rows" if tile_rows > 0
+             else ("k_dirmatvec_x2" if tile_rows in (-2, -3, -4) else "k_dirmatvec"))
     names = ["proj_dots", hname, "k_scalars", "k_update_dots", "none"]
     dom = 1 if ks[1] >= ks[3] else 3
     pk = peaks()
@@ -315,25 +369,27 @@ def run_ours(args, wl):
                     algorithmic_bytes=float(kb[dom]),
                     cocg_share=float(ks[dom] / max(1e-30, sum(ks))))
 
-    # FP64 form on the same workload (its own seeded sample) and the mixed-vs-FP64 error
+    # FP64 form and mixed form timed on one and the same seeded sample, and the
+    # mixed-vs-FP64 error on it
     fp64 = None
     if not args.no_fp64:
         c64 = context("fp64")
-        sel, fq = sample_probes(P, wl["nw"], args.fp64_probes_per_freq, seed0 + 7)
+        sel, fq = sample(args.fp64_probes_per_freq, seed0 + 7)
         pr = probe_idx[torch.from_numpy(sel).to(dev)]
         fqt = torch.from_numpy(fq).to(dev)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        with torch.cuda.stream(stream):
-            o64 = R.rpa_probe_density(c64.ctx, pr, fqt, allow_nonconv=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t64 = e0.elapsed_time(e1) * 1e-3
-        with torch.cuda.stream(stream):
-            omx = R.rpa_probe_density(cm.ctx, pr, fqt, allow_nonconv=True)
-        torch.cuda.synchronize()
+
+        def timed(c):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                o = R.rpa_probe_density(c.ctx, pr, fqt, allow_nonconv=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return o, e0.elapsed_time(e1) * 1e-3
+        o64, t64 = timed(c64)
+        omx, tmx = timed(cm)
         dd = (omx["d"] - o64["d"]).cpu().numpy()
         g3 = nd / P
         # E_c difference estimated from the sample: per frequency the sampled mean of d_mix -
@@ -348,8 +404,14 @@ def run_ours(args, wl):
                 if m.sum() > 1:
                     var += (w[k] * P) ** 2 * dd[m].var(ddof=1) / m.sum()
         scale = g3 / (2 * np.pi) / nat
-        fp64 = dict(value=len(sel) / t64, unit="probe-pts/s", probe_points=int(len(sel)),
-                    seconds=t64, mixed_speedup=(value / world) / (len(sel) / t64),
+        fp64 = dict(value=world * len(sel) / t64, unit="probe-pts/s",
+                    probe_points=int(len(sel)), seconds=t64,
+                    mixed_value_same_sample=world * len(sel) / tmx, mixed_seconds=tmx,
+                    mixed_speedup=t64 / tmx,
+                    sample=(f"{args.fp64_probes_per_freq} seeded coarse points per frequency "
+                            "per rank, both forms on the same points"),
+                    nonconv_solves=dict(fp64=o64["stats"]["nonconv_solves"],
+                                        mixed=omx["stats"]["nonconv_solves"]),
                     ec_diff_mha_per_atom_est=1e3 * abs(est) * scale,
                     ec_diff_mha_per_atom_stderr=(1e3 * np.sqrt(var) * scale
                                                  if args.fp64_probes_per_freq > 1 else None),
@@ -369,7 +431,7 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(args.e2e_steps):
-            sel, fq = sample_probes(P, wl["nw"], per, seed0 + 500 + i)
+            sel, fq = sample(per, seed0 + 500 + i)
             pr_h = R.rpa_probe_indices(cm.ctx)[sel]
             R.rpa_set_potential(cm.ctx, vloc_h)
             R.rpa_set_projectors(cm.ctx, grp)
@@ -384,9 +446,12 @@ def run_ours(args, wl):
         e2e = dict(value=world * args.e2e_steps * len(sel) / te, unit="probe-pts/s",
                    h2d_bytes_per_step=int(h2d_step), d2h_bytes_per_step=int(d2h_step))
 
-    cpu = None
+    # the oracle on the host cores: CPU baseline and the error of both GPU forms against it
+    cpu, oracle_err = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(s, wl, om, R.rpa_probe_indices(cm.ctx))
+        cpu, oprobes, d_ref = oracle_leg(s, wl, om, R.rpa_probe_indices(cm.ctx))
+        with torch.cuda.stream(stream):
+            oracle_err = oracle_error(R, context, wl, om, w, oprobes, d_ref, P, nd, nat)
 
     st0 = stats[0] if stats else {}
     tot_iters = sum(st["cocg_iters"] for st in stats)
@@ -414,7 +479,11 @@ def run_ours(args, wl):
         cocg=dict(mean_iters=tot_iters / max(1, tot_solves), solves=tot_solves,
                   max_iters=max(st["max_cocg_iters"] for st in stats) if stats else 0,
                   refine_rounds=sum(st["refine_rounds"] for st in stats),
-                  solves_per_s=world * tot_solves / t, iters_per_s=world * tot_iters / t),
+                  solves_per_s=world * tot_solves / t, iters_per_s=world * tot_iters / t,
+                  nonconv_solves=sum(st["nonconv_solves"] for st in stats),
+                  breakdown_solves=sum(st["breakdown_solves"] for st in stats),
+                  step_statuses=sorted(set(statuses))),
+        oracle_error=oracle_err,
         phases_s=list(np.sum([st["seconds_phase"] for st in stats], axis=0)) if stats else None,
     )
     if rank == 0:
@@ -424,8 +493,86 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+def run_interp_sweep(args, wl):
+    """Interpolation study (Section 3.2 operators, Section 5.2 metrics) on the workload's cell:
+    strides g = 2, 3 x {trilinear, tricubic} x {TF32x3, BF16} projection, against densities
+    computed directly at a seeded sample of fine points that are not coarse points (FP64
+    form, stride 1, Sternheimer tol 1e-8).  The interpolants are local, so d is computed only
+    at the coarse points within 2g of a sample point (every 4-point stencil lies there) and
+    the rest of the coarse array stays zero.  One frequency (the middle node) and N_l steps;
+    Fourier interpolation needs the whole coarse array and is left out.  Prints one JSON line
+    per variant with the wall time of its coarse probe-points and |dE|, L1 and ECR over the
+    sample, plus the E_c error the sample implies for that frequency's term."""
+    import torch
+
+    import paper_2609_16408_gb300 as R
+    torch.cuda.set_device(0)
+    s = make_system(wl["system"])
+    om, w = R.rpa_gl_frequencies(wl["nw"])
+    km = wl["nw"] // 2
+    nl = args.sweep_nl
+    n = s.n
+    nd = s.N_d
+    rng = np.random.default_rng(2609)
+    fine = []
+    while len(fine) < args.sweep_points:
+        x = rng.integers(0, n[0]), rng.integers(0, n[1]), rng.integers(0, n[2])
+        if all(c % 6 != 0 for c in x):  # on no coarse node for g = 2 or 3
+            fine.append(x)
+    fine = np.array(fine)
+    fidx = (fine[:, 0] + n[0] * (fine[:, 1] + n[1] * fine[:, 2])).astype(np.int64)
+
+    def ctx(prec, g, interp="cubic", proj="tf32x3", tol=wl["tol"]):
+        form = prec if prec == "fp64" else ("mixed_bf16" if proj == "bf16" else "mixed")
+        return R.Context.from_system(s, om, w, lanczos_max=nl, stern_tol=tol,
+                                     stern_maxit=20000, precision=form, stride=(g, g, g),
+                                     interp=interp, refine=args.refine)
+    c1 = ctx("fp64", 1, interp="none", tol=1e-8)
+    ref = np.asarray(R.rpa_probe_density(c1.ctx, fidx, np.full(len(fidx), km, np.int32))["d"])
+    c1.close()
+    for g in (2, 3):
+        for proj in ("tf32x3", "bf16"):
+            c = ctx("mixed", g, proj=proj)
+            P = R.rpa_num_probes(c.ctx)
+            cidx = R.rpa_probe_indices(c.ctx)
+            cc = np.stack([cidx % n[0], (cidx // n[0]) % n[1], cidx // (n[0] * n[1])], axis=1)
+            near = np.zeros(P, dtype=bool)
+            for f in fine:
+                dist = np.abs(cc - f[None, :])
+                dist = np.minimum(dist, np.asarray(n)[None, :] - dist)  # periodic distance
+                near |= np.all(dist < 2 * g, axis=1)
+            sel = np.nonzero(near)[0]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = R.rpa_probe_density(c.ctx, cidx[sel].astype(np.int64),
+                                      np.full(len(sel), km, np.int32), allow_nonconv=True)
+            tsec = time.perf_counter() - t0
+            dco = np.zeros((wl["nw"], P))
+            dco[km, sel] = out["d"]
+            for kind in ("linear", "cubic"):
+                R.rpa_set_options(c.ctx, c.opts, interp=kind)
+                dfi, _ = R.rpa_interpolate(c.ctx, dco, nd)
+                dd = np.asarray(dfi)[km, fidx] - ref
+                s_ = abs(float(dd.sum()))
+                l1 = float(np.abs(dd).sum())
+                ec_est = (nd / len(fidx)) * float(dd.sum()) * w[km] / (2 * np.pi) / wl["natom"]
+                line = dict(sweep="interpolation", workload=wl["system"], stride=g,
+                            interp=kind, projection=proj, frequency=float(om[km]),
+                            lanczos_steps=nl, stern_tol=wl["tol"],
+                            coarse_probe_points=int(len(sel)), seconds=tsec,
+                            probe_pts_per_s=len(sel) / tsec, full_coarse_points=int(P),
+                            sample_points=int(len(fidx)), abs_err=s_, l1=l1,
+                            ecr=s_ / l1 if l1 > 0 else 0.0,
+                            max_rel_err=float(np.max(np.abs(dd) / np.abs(ref))),
+                            ec_err_mha_per_atom_est=1e3 * abs(ec_est),
+                            status=int(out["status"]))
+                print(json.dumps(line), flush=True)
+            c.close()
+
+
 _KERNEL_FILES = {"k_dirmatvec": "cocg_fused.cu", "k_update_dots": "cocg_fused.cu",
-                 "k_dirmatvec_x2": "cocg_x2.cu", "k_dirmatvec_rows": "cocg_rows.cu"}
+                 "k_dirmatvec_x2": "cocg_x2.cu", "k_dirmatvec_rows": "cocg_rows.cu",
+                 "k_dirmatvec_band": "cocg_band.cu"}
 
 
 def kernel_source_sha(kernel="k_dirmatvec"):
@@ -461,13 +608,19 @@ def main():
                     help="override the frequency count (small profiling cases only)")
     ap.add_argument("--tile", type=int, default=-1,
                     help="H-apply tiling of the mixed form: -1 autotune, 0 32x8 column tiles, "
-                         "-2 64x8 two-point tiles, h > 0 full-row tiles of height h")
+                         "-2 64x8 two-point tiles, h > 0 full-row tiles of height h, -100-h "
+                         "bands of h full rows (asynchronous-copy pipeline)")
     ap.add_argument("--proj", default="tf32x3", choices=["tf32x3", "bf16"],
                     help="operand form of the mixed form's projection GEMMs")
     ap.add_argument("--stride", type=int, default=0,
                     help="override the coarse stride g on every axis (interpolation sweep)")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="replay COCG chunks as captured CUDA graphs (1) or launch directly (0)")
+    ap.add_argument("--sweep-interp", action="store_true",
+                    help="interpolation study instead of the benchmark line (strides 2, 3 x "
+                         "trilinear, tricubic x TF32x3, BF16 projection), one JSON line each")
+    ap.add_argument("--sweep-nl", type=int, default=3, help="Lanczos steps of the sweep")
+    ap.add_argument("--sweep-points", type=int, default=6, help="fine sample points")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -486,6 +639,9 @@ def main():
         if int(os.environ.get("RANK", "0")) != 0:
             return
         run_reference(args, wl)
+        return
+    if args.sweep_interp:
+        run_interp_sweep(args, wl)
         return
     run_ours(args, wl)
 
