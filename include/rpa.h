@@ -99,7 +99,9 @@ typedef struct {
   int tile;              /* xy tiling of the fused H-apply kernel: -1 = autotune (time the
                             candidate tilings on the first COCG solve of each precision and
                             keep the fastest), 0 = 32 x 8 column tiles, -2 = 64 x 8 tiles with
-                            two x points per thread (mixed form, even nx), h > 0 = tiles of h
+                            two x points per thread (mixed form, even nx), -3 / -4 = the same
+                            with each thread's z window in a shared-memory ring instead of
+                            registers (one / two centre-plane buffers), h > 0 = tiles of h
                             full x rows (needs nx <= 64), -100 - h = bands of h full x rows with
                             two points per thread and a multi-stage asynchronous copy pipeline
                             (mixed form, even nx <= 64, h divides ny); RPA_EINVAL if it does not

@@ -524,7 +524,7 @@ static void set_tiling(const rpa_ctx* c, FusedBufs<T>& fb, int ty, int nact) {
   fb.band_ty = is_band(ty) ? band_rows(ty) : 0;
   fb.ntiles_xy = is_band(ty) ? c->grid.n[1] / band_rows(ty)
                  : ty > 0    ? (c->grid.n[1] + ty - 1) / ty
-                             : (ty == kTileX2 ? x2_tiles_xy(c->grid.n[0], c->grid.n[1])
+                             : (is_x2(ty) ? x2_tiles_xy(c->grid.n[0], c->grid.n[1])
                                               : fused_ntiles_xy(c));
   const int nz = c->grid.n[2], R = c->grid.fd_radius;
   const int base = fused_zchunk(c);
@@ -560,7 +560,11 @@ static rpa_status choose_tiling(rpa_ctx* c, const CocgView<T>& cv, const FusedBu
     int cand[26];
     int nc = 0;
     cand[nc++] = 0;
-    if (sizeof(T) == 4 && x2_tile_fits(c->grid.n[0], c->grid.fd_radius)) cand[nc++] = kTileX2;
+    if (sizeof(T) == 4 && x2_tile_fits(c->grid.n[0], c->grid.fd_radius)) {
+      cand[nc++] = kTileX2;
+      cand[nc++] = kTileX2Ring1;
+      cand[nc++] = kTileX2Ring2;
+    }
     if (sizeof(T) == 4) {
       int bty[8];
       const int nb = band_candidates(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, c->ngroup,
@@ -639,6 +643,7 @@ static rpa_status run_chunk_graph(rpa_ctx* c, const CocgView<T>& cv, const Fused
   if (!hit) {
     if (fb.row_ty > 0) CK(launch_dirmatvec_rows_prepare<T>());  // attributes before capture
     if (is_band(fb.row_ty)) CK(launch_dirmatvec_band_prepare());
+    if (is_x2(fb.row_ty) && fb.row_ty != kTileX2) CK(launch_dirmatvec_x2_prepare());
     if (c->graphs.size() >= 64) {  // bounded cache: drop the oldest
       if (c->graphs.front().exec) cudaGraphExecDestroy(c->graphs.front().exec);
       c->graphs.erase(c->graphs.begin());
@@ -1576,7 +1581,7 @@ rpa_status rpa_set_options(rpa_ctx* c, const rpa_options* o) {
     return fail(c, RPA_EINVAL, "bad option");
   for (int a = 0; a < 3; ++a)
     if (o->stride[a] < 1 || o->stride[a] > c->grid.n[a]) return fail(c, RPA_EINVAL, "bad stride");
-  if (o->tile == kTileX2) {
+  if (is_x2(o->tile)) {
     if (o->precision == RPA_FP64 || !x2_tile_fits(c->grid.n[0], c->grid.fd_radius))
       return fail(c, RPA_EINVAL, "two-point tiles need the mixed form and an even nx");
   } else if (is_band(o->tile)) {
@@ -1590,7 +1595,7 @@ rpa_status rpa_set_options(rpa_ctx* c, const rpa_options* o) {
                         ? row_tile_fits<double>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, o->tile)
                         : row_tile_fits<float>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, o->tile);
     if (!ok) return fail(c, RPA_EINVAL, "row-tile height does not fit this grid");
-  } else if (o->tile < -2) {  // -3 .. -100
+  } else if (o->tile < -2) {  // -5 .. -100
     return fail(c, RPA_EINVAL, "bad tile option");
   }
   if (o->graphs != 0 && o->graphs != 1) return fail(c, RPA_EINVAL, "bad graphs option");

@@ -369,7 +369,7 @@ cudaError_t launch_dirmatvec_only(const CocgView<T>& cv, const FusedBufs<T>& fb,
       return cudaErrorInvalidValue;  // FP32 only
     }
   }
-  if (fb.row_ty == kTileX2) {
+  if (is_x2(fb.row_ty)) {
     if constexpr (sizeof(T) == 4) {
       cudaError_t e = launch_dirmatvec_x2(cv, fb, s);
       note_launch();

@@ -23,6 +23,13 @@ struct FusedBufs {
 };
 
 constexpr int kTileX2 = -2;
+// the two-point tiles with the z window in a shared-memory ring (see cocg_x2.cu): one centre
+// plane buffer (three blocks per SM) or two
+constexpr int kTileX2Ring1 = -3, kTileX2Ring2 = -4;
+inline bool is_x2(int code) {
+  return code == kTileX2 || code == kTileX2Ring1 || code == kTileX2Ring2;
+}
+cudaError_t launch_dirmatvec_x2_prepare();
 // tiling codes of the band kernel: -100 - h for bands of h rows
 constexpr int kTileBandBase = -100;
 inline int band_code(int ty) { return kTileBandBase - ty; }

@@ -10,6 +10,8 @@
 // on a 16-byte boundary.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "cocg.cuh"
 #include "cocg_fused.cuh"
 #include "fused_dev.cuh"
@@ -27,21 +29,39 @@ __device__ __forceinline__ void st4(cpx<float>* p, const cpx<float>& a, const cp
   *reinterpret_cast<float4*>(p) = make_float4(a.re, a.im, b.re, b.im);
 }
 
-template <int R, bool FIRST, bool SMEM_CD>
-__global__ void __launch_bounds__(kX2Threads, 2)
-    k_dirmatvec_x2(CocgView<float> cv, FusedBufs<float> fb) {
+// Where the 2R+1 values of a thread's z window live (ZM):
+//   kZRegs   registers, rotated by one plane per step (the original form);
+//   kZRing1  a per-thread ring in shared memory (slot = plane mod 2R+1, read at offsets fixed
+//            per plane), one centre-plane buffer (two barriers per plane): no register queue,
+//            so three blocks fit an SM;
+//   kZRing2  the same ring with two centre-plane buffers (one barrier per plane).
+// Only the thread that owns a column reads and writes its ring slots, so the ring needs no
+// barrier of its own.
+constexpr int kZRegs = 0, kZRing1 = 1, kZRing2 = 2;
+
+template <int R>
+constexpr size_t x2_ring_bytes() {
+  return (size_t)(2 * R + 1) * kX2Threads * sizeof(float4);
+}
+
+template <int R, bool FIRST, bool SMEM_CD, int ZM>
+__global__ void __launch_bounds__(kX2Threads, ZM == kZRing1 ? 3 : 2)
+    k_dirmatvec_x2(CocgView<float> cv, FusedBufs<float> fb, int ring_off) {
   using T = float;
   const int s = cv.list ? cv.list[blockIdx.y] : blockIdx.y;
   if (s < 0 || cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
+  constexpr bool RING = ZM != kZRegs;
+  constexpr int NQ = 2 * R + 1;
   constexpr int XO = R + (R & 1);             // x offset of the tile in the plane (even)
   constexpr int EXN = kX2TX + 2 * XO, EYN = kX2TY + 2 * R;
   constexpr int PLN = EXN * EYN;
   constexpr int NUSED = (kX2TX + 2 * R) * EYN;  // used slots (tile + halo)
   constexpr int NHALO = NUSED - kX2TX * kX2TY;
   constexpr int HPT = (NHALO + kX2Threads - 1) / kX2Threads;
-  __shared__ __align__(16) cpx<T> pl[2 * PLN];
+  __shared__ __align__(16) cpx<T> pl[(ZM == kZRing1 ? 1 : 2) * PLN];
   __shared__ T sh[8 * 2];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
+  float4* ring = reinterpret_cast<float4*>(dyn_smem + ring_off);  // NQ x kX2Threads (RING)
   const Stencil<T>& st = cv.st;
   const int nx = st.nx, ny = st.ny, nz = st.nz;
   const int plane = nx * ny;
@@ -135,14 +155,22 @@ __global__ void __launch_bounds__(kX2Threads, 2)
       if (!FIRST) pv = po[q];
     }
   };
-  cpx<T> za[2 * R + 1], zb[2 * R + 1];  // z queues of the two columns
+  constexpr int QL = RING ? 1 : 2 * R + 1;
+  cpx<T> za[QL], zb[QL];  // z queues of the two columns (register form)
+  // ring slot of plane zz (zz >= z0 - R)
+  auto rslot = [&](int zz) -> int { return (zz - z0 + R) % NQ; };
 #pragma unroll
   for (int i = 0; i < 2 * R; ++i) {
     const int zo = zoff(z0 - R + i);
     cpx<T> r0, r1, p0, p1;
     ld2((zo < 0 || own_xy < 0) ? -1 : zo + own_xy, r0, r1, p0, p1);
-    za[i] = comb(r0, p0);
-    zb[i] = comb(r1, p1);
+    const cpx<T> va = comb(r0, p0), vb = comb(r1, p1);
+    if constexpr (RING) {
+      ring[i * kX2Threads + threadIdx.x] = make_float4(va.re, va.im, vb.re, vb.im);
+    } else {
+      za[i] = va;
+      zb[i] = vb;
+    }
   }
   cpx<T> nr0, nr1, np0, np1, h_r[HPT], h_p[HPT];
   const bool has_nl = cv.nl.ngroup > 0;
@@ -186,10 +214,25 @@ __global__ void __launch_bounds__(kX2Threads, 2)
   A acc_re = 0, acc_im = 0;
   const T c0 = st.c0;
   for (int z = z0; z < z1; ++z) {
-    const int bo = ((z - z0) & 1) * PLN;
-    za[2 * R] = comb(nr0, np0);
-    zb[2 * R] = comb(nr1, np1);
-    st4(pl + bo + own_slot, za[R], zb[R]);
+    const int bo = ZM == kZRing1 ? 0 : ((z - z0) & 1) * PLN;
+    cpx<T> c, d;  // this column's values at plane z
+    int rb = 0;   // ring slot of plane z
+    if constexpr (RING) {
+      rb = rslot(z);
+      const cpx<T> va = comb(nr0, np0), vb = comb(nr1, np1);
+      const int sn = rb + R < NQ ? rb + R : rb + R - NQ;  // slot of plane z + R
+      ring[sn * kX2Threads + threadIdx.x] = make_float4(va.re, va.im, vb.re, vb.im);
+      const float4 cc = ring[rb * kX2Threads + threadIdx.x];
+      c = mk<T>(cc.x, cc.y);
+      d = mk<T>(cc.z, cc.w);
+      if (ZM == kZRing1 && z > z0) __syncthreads();  // everyone is done with plane z - 1
+    } else {
+      za[2 * R] = comb(nr0, np0);
+      zb[2 * R] = comb(nr1, np1);
+      c = za[R];
+      d = zb[R];
+    }
+    st4(pl + bo + own_slot, c, d);
 #pragma unroll
     for (int k = 0; k < HPT; ++k)
       if (halo_slot[k] >= 0) pl[bo + halo_slot[k]] = comb(h_r[k], h_p[k]);
@@ -198,7 +241,6 @@ __global__ void __launch_bounds__(kX2Threads, 2)
     __syncthreads();
     if (valid) {
       const int q = own_xy + z * plane;
-      const cpx<T> c = za[R], d = zb[R];
       const cpx<T>* cs = pl + bo + own_slot;
       const float2 vv = *reinterpret_cast<const float2*>(vloc + q);  // q even: 8-byte aligned
       const T dg0 = c0 + vv.x, dg1 = c0 + vv.y;
@@ -221,8 +263,17 @@ __global__ void __launch_bounds__(kX2Threads, 2)
         const float4 up = ld4(cs - m * EXN), dn = ld4(cs + m * EXN);
         a0 = caxpy_r(a0, st.cy[m], mk<T>(up.x + dn.x, up.y + dn.y));
         a1 = caxpy_r(a1, st.cy[m], mk<T>(up.z + dn.z, up.w + dn.w));
-        a0 = caxpy_r(a0, st.cz[m], cadd(za[R - m], za[R + m]));
-        a1 = caxpy_r(a1, st.cz[m], cadd(zb[R - m], zb[R + m]));
+        if constexpr (RING) {
+          const int sl = rb - m >= 0 ? rb - m : rb - m + NQ;
+          const int sh_ = rb + m < NQ ? rb + m : rb + m - NQ;
+          const float4 lo = ring[sl * kX2Threads + threadIdx.x];
+          const float4 hi = ring[sh_ * kX2Threads + threadIdx.x];
+          a0 = caxpy_r(a0, st.cz[m], mk<T>(lo.x + hi.x, lo.y + hi.y));
+          a1 = caxpy_r(a1, st.cz[m], mk<T>(lo.z + hi.z, lo.w + hi.w));
+        } else {
+          a0 = caxpy_r(a0, st.cz[m], cadd(za[R - m], za[R + m]));
+          a1 = caxpy_r(a1, st.cz[m], cadd(zb[R - m], zb[R + m]));
+        }
       }
       a0 = proj(a0, e0, e1);
       a1 = proj(a1, e1, e2);
@@ -231,10 +282,12 @@ __global__ void __launch_bounds__(kX2Threads, 2)
       acc_re += (A)c.re * a0.re - (A)c.im * a0.im + (A)d.re * a1.re - (A)d.im * a1.im;
       acc_im += (A)c.re * a0.im + (A)c.im * a0.re + (A)d.re * a1.im + (A)d.im * a1.re;
     }
+    if constexpr (!RING) {
 #pragma unroll
-    for (int i = 0; i < 2 * R; ++i) {
-      za[i] = za[i + 1];
-      zb[i] = zb[i + 1];
+      for (int i = 0; i < 2 * R; ++i) {
+        za[i] = za[i + 1];
+        zb[i] = zb[i + 1];
+      }
     }
   }
   A acc2[2] = {acc_re, acc_im};
@@ -248,24 +301,74 @@ __global__ void __launch_bounds__(kX2Threads, 2)
   }
 }
 
-template <int R>
-void launch_r(const CocgView<float>& cv, const FusedBufs<float>& fb, cudaStream_t s) {
+template <int R, int ZM>
+void launch_zm(const CocgView<float>& cv, const FusedBufs<float>& fb, cudaStream_t s) {
   constexpr int XO = R + (R & 1);
-  constexpr size_t kPlanes = 2 * sizeof(cpx<float>) * (kX2TX + 2 * XO) * (kX2TY + 2 * R);
+  constexpr size_t kPlanes = (ZM == kZRing1 ? 1 : 2) * sizeof(cpx<float>) * (kX2TX + 2 * XO) *
+                             (kX2TY + 2 * R);
   size_t cdb = fb.cd_in_smem ? sizeof(cpx<float>) * cv.nl.ngroup * kProjChunk : 0;
-  if (cdb + kPlanes + 1024 > 48 * 1024) cdb = 0;
+  if (ZM == kZRegs) {
+    if (cdb + kPlanes + 1024 > 48 * 1024) cdb = 0;  // static + dynamic within 48 KB
+  } else if (cdb > 8 * 1024) {
+    cdb = 0;  // the ring forms stage at most 8 KB of coefficients next to the ring
+  }
+  const int ring_off = (int)((cdb + 15) / 16 * 16);
+  const size_t dyn = ZM == kZRegs ? cdb : ring_off + x2_ring_bytes<R>();
   const dim3 grid(fb.ntiles_xy, fb.nact, fb.nzchunk);
   if (fb.first) {
     if (cdb)
-      k_dirmatvec_x2<R, true, true><<<grid, kX2Threads, cdb, s>>>(cv, fb);
+      k_dirmatvec_x2<R, true, true, ZM><<<grid, kX2Threads, dyn, s>>>(cv, fb, ring_off);
     else
-      k_dirmatvec_x2<R, true, false><<<grid, kX2Threads, 0, s>>>(cv, fb);
+      k_dirmatvec_x2<R, true, false, ZM><<<grid, kX2Threads, dyn, s>>>(cv, fb, ring_off);
   } else {
     if (cdb)
-      k_dirmatvec_x2<R, false, true><<<grid, kX2Threads, cdb, s>>>(cv, fb);
+      k_dirmatvec_x2<R, false, true, ZM><<<grid, kX2Threads, dyn, s>>>(cv, fb, ring_off);
     else
-      k_dirmatvec_x2<R, false, false><<<grid, kX2Threads, 0, s>>>(cv, fb);
+      k_dirmatvec_x2<R, false, false, ZM><<<grid, kX2Threads, dyn, s>>>(cv, fb, ring_off);
   }
+}
+
+template <int R>
+void launch_r(const CocgView<float>& cv, const FusedBufs<float>& fb, cudaStream_t s) {
+  if (fb.row_ty == kTileX2Ring1)
+    launch_zm<R, kZRing1>(cv, fb, s);
+  else if (fb.row_ty == kTileX2Ring2)
+    launch_zm<R, kZRing2>(cv, fb, s);
+  else
+    launch_zm<R, kZRegs>(cv, fb, s);
+}
+
+// opt-in dynamic shared memory of the ring forms, once per device
+cudaError_t x2_attr() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return cudaSuccess;
+  constexpr int kMax = 96 * 1024;
+#define RPA_X2_ATTR(RR, ZZ)                                                                   \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(k_dirmatvec_x2<RR, true, true, ZZ>,                             \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);             \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(k_dirmatvec_x2<RR, true, false, ZZ>,                            \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);             \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(k_dirmatvec_x2<RR, false, true, ZZ>,                            \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);             \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(k_dirmatvec_x2<RR, false, false, ZZ>,                           \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
+#define RPA_X2_ATTR_R(RR) RPA_X2_ATTR(RR, kZRing1) RPA_X2_ATTR(RR, kZRing2)
+  RPA_X2_ATTR_R(1) RPA_X2_ATTR_R(2) RPA_X2_ATTR_R(3) RPA_X2_ATTR_R(4)
+  RPA_X2_ATTR_R(5) RPA_X2_ATTR_R(6) RPA_X2_ATTR_R(7) RPA_X2_ATTR_R(8)
+#undef RPA_X2_ATTR_R
+#undef RPA_X2_ATTR
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
 }
 
 }  // namespace
@@ -276,8 +379,14 @@ int x2_tiles_xy(int nx, int ny) {
   return ((nx + kX2TX - 1) / kX2TX) * ((ny + kX2TY - 1) / kX2TY);
 }
 
+cudaError_t launch_dirmatvec_x2_prepare() { return x2_attr(); }
+
 cudaError_t launch_dirmatvec_x2(const CocgView<float>& cv, const FusedBufs<float>& fb,
                                 cudaStream_t s) {
+  if (fb.row_ty == kTileX2Ring1 || fb.row_ty == kTileX2Ring2) {
+    cudaError_t e = x2_attr();
+    if (e != cudaSuccess) return e;
+  }
   switch (cv.st.R) {
     case 1: launch_r<1>(cv, fb, s); break;
     case 2: launch_r<2>(cv, fb, s); break;

@@ -109,7 +109,8 @@ def test_chi0_mixed(name):
 
 @pytest.mark.parametrize("name,tile", [("per", 0), ("per", 1), ("per", 4), ("per", 11),
                                        ("dir", 3), ("dir", 10), ("mix", 2), ("mix", 9),
-                                       ("per", -2), ("mix", -2), ("per", -111), ("mix", -109)])
+                                       ("per", -2), ("mix", -2), ("per", -111), ("mix", -109),
+                                       ("per", -3), ("mix", -4)])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_chi0_tilings(name, tile, prec):
     """Every H-apply tiling (32 x 8 column tiles, 64 x 8 two-point tiles, full-row tiles of
@@ -117,7 +118,7 @@ def test_chi0_tilings(name, tile, prec):
     tiles, halos larger than the tile, periodic wrap inside a tile, an x axis shorter than
     twice the padding so that edge pairs wrap to both sides, zero-filled Dirichlet halo rows)
     gives the oracle's chi0 u."""
-    if tile in (-2, -111, -109) and prec == "fp64":
+    if tile in (-2, -3, -4, -111, -109) and prec == "fp64":
         pytest.skip("two-point and band tiles are FP32 kernels")
     s = sysfix(name)
     tol = 1e-12 if prec == "fp64" else 1e-10
@@ -140,7 +141,7 @@ def test_tile_option_checked():
     with pytest.raises(RuntimeError):
         R.rpa_set_options(c.ctx, precision="fp64", tile=12)  # taller than the grid
     with pytest.raises(RuntimeError):
-        R.rpa_set_options(c.ctx, tile=-3)
+        R.rpa_set_options(c.ctx, tile=-5)
     with pytest.raises(RuntimeError):
         R.rpa_set_options(c.ctx, precision="fp64", tile=-2)  # FP32 kernel only
     with pytest.raises(RuntimeError):
