@@ -263,7 +263,7 @@ def run_ours(args, wl):
                           stern_maxit=20000, precision=mixed_form if prec == "mixed" else prec,
                           stride=wl["stride"], interp=wl["interp"], refine=args.refine,
                           profile=profile, tile=tile if prec != "fp64" else -1,
-                          graphs=args.graphs, inner_tol=args.inner_tol)
+                          graphs=args.graphs, inner_tol=args.inner_tol, lanes=args.lanes)
         return c
 
     cm = context("mixed", tile=args.tile)
@@ -614,6 +614,8 @@ def main():
                     help="operand form of the mixed form's projection GEMMs")
     ap.add_argument("--stride", type=int, default=0,
                     help="override the coarse stride g on every axis (interpolation sweep)")
+    ap.add_argument("--lanes", type=int, default=1,
+                    help="probe-point lanes run concurrently (options.lanes)")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="replay COCG chunks as captured CUDA graphs (1) or launch directly (0)")
     ap.add_argument("--sweep-interp", action="store_true",

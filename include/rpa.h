@@ -125,6 +125,14 @@ typedef struct {
                             MMA is issued; the call then returns RPA_ETIMEOUT with the tensor
                             memory freed and the context usable, so the bounded-wait failure
                             path can be tested without a GPU fault */
+  int lanes;             /* 1 (default): the probe-points of a call run in waves one after
+                            the other.  k in 2..8 (scalar Lanczos only): they are dealt
+                            round-robin to k lanes that run concurrently, each with its own
+                            CUDA stream, workspace and host thread (k - 1 helper contexts
+                            created from this context's inputs on first use, dropped when an
+                            input or option changes), so that the latency-bound COCG tail of
+                            one lane overlaps the others' work; waves are sized from 1/k of
+                            the free memory each.  Results and statistics are as for k = 1 */
 } rpa_options;
 
 typedef struct {

@@ -99,7 +99,7 @@ class Options(C.Structure):
                 ("fkind", C.c_int), ("refine", C.c_int), ("inner_tol", C.c_double),
                 ("profile", C.c_int), ("tile", C.c_int), ("graphs", C.c_int),
                 ("lanczos_block", C.c_int), ("refine_restart", C.c_int),
-                ("debug_expire_waits", C.c_int)]
+                ("debug_expire_waits", C.c_int), ("lanes", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -113,6 +113,14 @@ struct rpa_ctx {
   // RPA_EBREAKDOWN (the more severe is kept), with its reason
   rpa_status soft = RPA_OK;
   std::string soft_msg;
+  // probe-point lanes (options.lanes > 1): helper contexts with their own stream and
+  // workspace, set up from this context's inputs on first use and dropped when an input
+  // changes; the projector inputs are kept on the host for them
+  std::vector<rpa_ctx*> lanes;
+  int hp_ng = 0;
+  std::vector<int> hp_nnz, hp_nproj, hp_idx;
+  std::vector<double> hp_chi, hp_gamma;
+  double mem_share = 1.0;  // share of the free device memory a wave may take
 };
 
 namespace rpa {
@@ -359,7 +367,7 @@ static int choose_batch(rpa_ctx* c, long long count) {
   if (nb <= 0) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = (size_t)8 << 30;
-    const size_t avail = (size_t)(0.55 * (double)fr);
+    const size_t avail = (size_t)(0.55 * c->mem_share * (double)fr);
     nb = (int)std::max<size_t>(1, avail / std::max<size_t>(1, per_probe_bytes(c)));
     nb = std::min(nb, 512);
   }
@@ -1133,6 +1141,11 @@ static rpa_status run_wave(rpa_ctx* c, int nb, const long long* probe_h, const d
   return RPA_OK;
 }
 
+static void drop_lanes(rpa_ctx* c) {
+  for (rpa_ctx* h : c->lanes) rpa_destroy(h);
+  c->lanes.clear();
+}
+
 // Run count probe-points in waves; d/alpha/beta/steps are host arrays in input order.
 static rpa_status run_probes(rpa_ctx* c, long long count, const long long* probe,
                              const double* omg, double* d, double* alpha, double* beta,
@@ -1198,6 +1211,143 @@ static rpa_status run_probes(rpa_ctx* c, long long count, const long long* probe
     o.beta = beta ? beta + s0 * nl : nullptr;
     o.steps = steps ? steps + s0 : nullptr;
     CKS(run_wave(c, nb, probe + s0, omg + s0, o, st));
+  }
+  return RPA_OK;
+}
+
+// helper contexts for options.lanes, set up from c's inputs (device copies on their own
+// streams; the 1-D eigenbases are recomputed by each helper)
+static rpa_status ensure_lanes(rpa_ctx* c, int k) {
+  if ((int)c->lanes.size() >= k - 1) return RPA_OK;
+  drop_lanes(c);
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < k - 1; ++i) {
+    rpa_ctx* h = nullptr;
+    rpa_status st = rpa_create(&h, &c->grid, nullptr);
+    if (st != RPA_OK) return fail(c, st, "creating a lane context failed");
+    c->lanes.push_back(h);
+    rpa_options o = c->opt;
+    o.lanes = 1;
+    if (st == RPA_OK) st = rpa_set_potential(h, c->d64.vloc.as<double>(), RPA_DEVICE);
+    if (st == RPA_OK)
+      st = rpa_set_projectors(h, c->hp_ng, c->hp_nnz.data(), c->hp_nproj.data(),
+                              c->hp_idx.data(), c->hp_chi.data(), c->hp_gamma.data());
+    if (st == RPA_OK)
+      st = rpa_set_occupied(h, c->ns, c->d64.psi.as<double>(), c->eps_d.as<double>(),
+                            RPA_DEVICE);
+    if (st == RPA_OK) st = rpa_set_frequencies(h, c->nw, c->omega.data(), c->weight.data());
+    if (st == RPA_OK) st = rpa_set_options(h, &o);
+    if (st != RPA_OK) {
+      const std::string m = h->err;
+      drop_lanes(c);
+      return fail(c, st, "setting up a lane context failed: " + m);
+    }
+    std::memcpy(h->tuned_ty, c->tuned_ty, sizeof(c->tuned_ty));
+  }
+  return RPA_OK;
+}
+
+static void add_stats(rpa_stats* a, const rpa_stats& b) {
+  for (int i = 0; i < 8; ++i) {
+    a->seconds_phase[i] += b.seconds_phase[i];
+    a->kernel_seconds[i] += b.kernel_seconds[i];
+    a->kernel_launches[i] += b.kernel_launches[i];
+    a->kernel_bytes[i] += b.kernel_bytes[i];
+  }
+  a->probe_points += b.probe_points;
+  a->matvecs += b.matvecs;
+  a->solves += b.solves;
+  a->cocg_iters += b.cocg_iters;
+  a->refine_rounds += b.refine_rounds;
+  a->nonconv_solves += b.nonconv_solves;
+  a->breakdown_solves += b.breakdown_solves;
+  a->max_cocg_iters = std::max(a->max_cocg_iters, b.max_cocg_iters);
+  a->lanczos_steps_max = std::max(a->lanczos_steps_max, b.lanczos_steps_max);
+  if (!a->precision_bytes) a->precision_bytes = b.precision_bytes;
+}
+
+// options.lanes = k > 1 (scalar Lanczos only): the probe-points are dealt round-robin to k
+// lanes -- this context and k - 1 helpers, each with its own stream and workspace and each
+// sizing its waves from 1/k of the free memory -- run concurrently from k host threads, so
+// that the COCG tail of one lane (few systems left, small latency-bound launches) overlaps
+// the other lanes' work.  Results return in input order; statistics are summed.
+static rpa_status run_probes_lanes(rpa_ctx* c, long long count, const long long* probe,
+                                   const double* omg, double* d, double* alpha, double* beta,
+                                   int* steps, rpa_stats* st) {
+  const int k = (int)std::min<long long>(c->opt.lanes, count);
+  if (k <= 1 || c->opt.lanczos_block > 1)
+    return run_probes(c, count, probe, omg, d, alpha, beta, steps, st);
+  CKS(ensure_lanes(c, k));
+  const int nl = c->opt.lanczos_max;
+  struct Part {
+    std::vector<long long> idx, pr;
+    std::vector<double> om, d, al, be;
+    std::vector<int> sp;
+    rpa_stats stats;
+    rpa_status rs = RPA_OK;
+  };
+  std::vector<Part> parts(k);
+  for (long long i = 0; i < count; ++i) {
+    Part& P = parts[i % k];
+    P.idx.push_back(i);
+    P.pr.push_back(probe[i]);
+    P.om.push_back(omg[i]);
+  }
+  std::vector<rpa_ctx*> ctx(k);
+  ctx[0] = c;
+  for (int l = 1; l < k; ++l) ctx[l] = c->lanes[l - 1];
+  for (int l = 0; l < k; ++l) {
+    Part& P = parts[l];
+    const size_t n = P.idx.size();
+    P.d.assign(n, 0.0);
+    if (alpha) P.al.assign(n * nl, 0.0);
+    if (beta) P.be.assign(n * nl, 0.0);
+    if (steps) P.sp.assign(n, 0);
+    std::memset(&P.stats, 0, sizeof(P.stats));
+    ctx[l]->mem_share = 1.0 / k;
+    ctx[l]->soft = RPA_OK;
+  }
+  rpa_stats* parent_prof = c->prof_stats;
+  std::vector<std::thread> th;
+  for (int l = 0; l < k; ++l)
+    th.emplace_back([&, l]() {
+      Part& P = parts[l];
+      rpa_ctx* h = ctx[l];
+      cudaSetDevice(h->device);
+      h->prof_stats = st ? &P.stats : nullptr;
+      P.rs = run_probes(h, (long long)P.idx.size(), P.pr.data(), P.om.data(), P.d.data(),
+                        alpha ? P.al.data() : nullptr, beta ? P.be.data() : nullptr,
+                        steps ? P.sp.data() : nullptr, st ? &P.stats : nullptr);
+      h->prof_stats = nullptr;
+    });
+  for (auto& t : th) t.join();
+  c->prof_stats = parent_prof;
+  for (int l = 0; l < k; ++l) ctx[l]->mem_share = 1.0;
+  for (int l = 0; l < k; ++l) {
+    if (parts[l].rs != RPA_OK) {
+      const std::string m = ctx[l]->err;
+      return l == 0 ? parts[0].rs : fail(c, parts[l].rs, "lane " + std::to_string(l) + ": " + m);
+    }
+  }
+  for (int l = 1; l < k; ++l)
+    if (ctx[l]->soft != RPA_OK) note_soft(c, ctx[l]->soft, ctx[l]->soft_msg.c_str());
+  if (c->tuned_ty[0][0] == -1) std::memcpy(c->tuned_ty, ctx[1]->tuned_ty, sizeof(c->tuned_ty));
+  for (int l = 0; l < k; ++l) {
+    const Part& P = parts[l];
+    for (size_t q = 0; q < P.idx.size(); ++q) {
+      const long long i = P.idx[q];
+      d[i] = P.d[q];
+      if (alpha) std::memcpy(alpha + i * nl, P.al.data() + q * nl, sizeof(double) * nl);
+      if (beta) std::memcpy(beta + i * nl, P.be.data() + q * nl, sizeof(double) * nl);
+      if (steps) steps[i] = P.sp[q];
+    }
+    if (st) {
+      add_stats(st, P.stats);
+      if (l == 0) {
+        st->tile_rows = P.stats.tile_rows;
+        st->tile_rows_tail = P.stats.tile_rows_tail;
+      }
+    }
   }
   return RPA_OK;
 }
@@ -1314,6 +1464,7 @@ rpa_status rpa_default_options(rpa_options* o) {
   o->lanczos_block = 1;
   o->refine_restart = 0;
   o->debug_expire_waits = 0;
+  o->lanes = 1;
   return RPA_OK;
 }
 
@@ -1378,6 +1529,7 @@ rpa_status rpa_create(rpa_ctx** out, const rpa_grid* g, void* stream) {
 
 void rpa_destroy(rpa_ctx* c) {
   if (!c) return;
+  drop_lanes(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->have_events)
     for (int i = 0; i < 8; ++i) cudaEventDestroy(c->ev[i]);
@@ -1399,6 +1551,7 @@ rpa_status rpa_set_potential(rpa_ctx* c, const double* vloc, int where) {
   CK(convert_d2f(c->d64.vloc.as<double>(), c->d32.vloc.as<float>(), c->nd, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->have_vloc = true;
+  drop_lanes(c);
   return RPA_OK;
 }
 
@@ -1511,6 +1664,20 @@ rpa_status rpa_set_projectors(rpa_ctx* c, int ngroups, const int* nnz, const int
     CK(cudaMemcpy(c->d32.coef.p, gcoef_f.data(), sizeof(float) * NG * kProjChunk, cudaMemcpyHostToDevice));
   }
   c->ngroup = NG;
+  // host copy of the inputs, for lane contexts
+  long long nidx = 0, nchi = 0, ngam = 0;
+  for (int g = 0; g < ngroups; ++g) {
+    nidx += nnz[g];
+    nchi += (long long)nproj[g] * nnz[g];
+    ngam += nproj[g];
+  }
+  c->hp_ng = ngroups;
+  c->hp_nnz.assign(nnz, nnz + ngroups);
+  c->hp_nproj.assign(nproj, nproj + ngroups);
+  c->hp_idx.assign(idx, idx + nidx);
+  c->hp_chi.assign(chi, chi + nchi);
+  c->hp_gamma.assign(gamma, gamma + ngam);
+  drop_lanes(c);
   return RPA_OK;
 }
 
@@ -1536,6 +1703,7 @@ rpa_status rpa_set_occupied(rpa_ctx* c, int ns, const double* psi, const double*
   c->ns = ns;
   c->have_occ = true;
   c->ws_nb = 0;
+  drop_lanes(c);
   return RPA_OK;
 }
 
@@ -1553,6 +1721,7 @@ rpa_status rpa_set_frequencies(rpa_ctx* c, int nw, const double* omega, const do
   CK(cudaMemcpy(c->weight_d.p, weight, sizeof(double) * nw, cudaMemcpyHostToDevice));
   c->nw = nw;
   c->have_freq = true;
+  drop_lanes(c);
   return RPA_OK;
 }
 
@@ -1599,6 +1768,7 @@ rpa_status rpa_set_options(rpa_ctx* c, const rpa_options* o) {
     return fail(c, RPA_EINVAL, "bad tile option");
   }
   if (o->graphs != 0 && o->graphs != 1) return fail(c, RPA_EINVAL, "bad graphs option");
+  if (o->lanes < 1 || o->lanes > 8) return fail(c, RPA_EINVAL, "lanes out of range");
   if (o->refine_restart != 0 && o->refine_restart != 1)
     return fail(c, RPA_EINVAL, "bad refine_restart option");
   if (o->debug_expire_waits != 0 && o->debug_expire_waits != 1)
@@ -1610,6 +1780,7 @@ rpa_status rpa_set_options(rpa_ctx* c, const rpa_options* o) {
   const bool realloc = o->precision != c->opt.precision || o->lanczos_max != c->opt.lanczos_max ||
                        o->refine != c->opt.refine;
   c->opt = *o;
+  drop_lanes(c);
   if (realloc) c->ws_nb = 0;
   return RPA_OK;
 }
@@ -1663,9 +1834,9 @@ rpa_status rpa_probe_density(rpa_ctx* c, int count, const long long* probe, cons
   std::vector<double> dh(count), ah(alpha ? (size_t)count * nl : 0), bh(beta ? (size_t)count * nl : 0);
   std::vector<int> sh(steps ? count : 0);
   c->soft = RPA_OK;
-  rpa_status rs = run_probes(c, count, pr.data(), om.data(), dh.data(),
-                             alpha ? ah.data() : nullptr, beta ? bh.data() : nullptr,
-                             steps ? sh.data() : nullptr, st);
+  rpa_status rs = run_probes_lanes(c, count, pr.data(), om.data(), dh.data(),
+                                   alpha ? ah.data() : nullptr, beta ? bh.data() : nullptr,
+                                   steps ? sh.data() : nullptr, st);
   c->prof_stats = nullptr;
   CKS(rs);
   CKS(copy_out(c, d, dh.data(), sizeof(double) * count, where));
@@ -1735,8 +1906,8 @@ rpa_status rpa_energy_density(rpa_ctx* c, double* d_coarse, double* d_fine, doub
       om[k * P + j] = c->omega[k];
     }
   c->soft = RPA_OK;
-  rpa_status rs = run_probes(c, count, pr.data(), om.data(), dh.data(), nullptr, nullptr,
-                             nullptr, st);
+  rpa_status rs = run_probes_lanes(c, count, pr.data(), om.data(), dh.data(), nullptr, nullptr,
+                                   nullptr, st);
   c->prof_stats = nullptr;
   CKS(rs);
   auto t1 = std::chrono::steady_clock::now();

@@ -513,6 +513,29 @@ def test_galerkin_projection_si8_tiles():
         assert np.all(np.abs(x0[i].imag - ref.imag) <= bim)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_lanes_match_single_pipeline(prec):
+    """options.lanes = 3: the probe-points dealt to three concurrent lanes (helper contexts
+    on their own streams) give the densities, tridiagonals and step counts of one pipeline,
+    in input order, with the statistics summed."""
+    s = sysfix("per")
+    probes = np.arange(5, s.N_d, 97, dtype=np.int64)[:11]
+    freqs = (np.arange(len(probes)) % 4).astype(np.int32)
+    out = {}
+    for lanes in (1, 3):
+        c, _, _ = ctx_for(s, precision=prec, lanczos_max=4, stern_tol=1e-10, stern_maxit=5000,
+                          lanes=lanes)
+        out[lanes] = R.rpa_probe_density(c.ctx, probes, freqs, nl=4, want_tridiag=True)
+        c.close()
+    a, b = out[1], out[3]
+    rt = 1e-9 if prec == "fp64" else 1e-6
+    assert np.allclose(a["d"], b["d"], rtol=rt, atol=0)
+    assert np.allclose(a["alpha"], b["alpha"], rtol=rt, atol=1e-14)
+    assert np.array_equal(a["steps"], b["steps"])
+    assert a["stats"]["probe_points"] == b["stats"]["probe_points"] == len(probes)
+    assert a["stats"]["solves"] == b["stats"]["solves"]
+
+
 def test_batch_energy_uneven_systems():
     """Systems of different grids and boundaries in one call equal their separate runs."""
     ctxs, refs = [], []
