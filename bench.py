@@ -263,7 +263,8 @@ def run_ours(args, wl):
                           stern_maxit=20000, precision=mixed_form if prec == "mixed" else prec,
                           stride=wl["stride"], interp=wl["interp"], refine=args.refine,
                           profile=profile, tile=tile if prec != "fp64" else -1,
-                          graphs=args.graphs, inner_tol=args.inner_tol, lanes=args.lanes)
+                          graphs=args.graphs, inner_tol=args.inner_tol, lanes=args.lanes,
+                          lanczos_block=args.lanczos_block if prec != "fp64" else 1)
         return c
 
     cm = context("mixed", tile=args.tile)
@@ -614,6 +615,9 @@ def main():
                     help="operand form of the mixed form's projection GEMMs")
     ap.add_argument("--stride", type=int, default=0,
                     help="override the coarse stride g on every axis (interpolation sweep)")
+    ap.add_argument("--lanczos-block", type=int, default=1,
+                    help="block Lanczos quadrature over blocks of this many probe-points of "
+                         "one frequency (options.lanczos_block; mixed form); 1 = scalar")
     ap.add_argument("--lanes", type=int, default=1,
                     help="probe-point lanes run concurrently (options.lanes)")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
