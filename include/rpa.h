@@ -213,6 +213,21 @@ rpa_status rpa_probe_indices(rpa_ctx *ctx, long long *idx);
 rpa_status rpa_energy_density(rpa_ctx *ctx, double *d_coarse, double *d_fine, double *ec,
                               rpa_stats *stats, int where);
 
+/* Checkpoint file of rpa_energy_density (path copied; NULL or "" turns it off, the
+ * default).  With a checkpoint, rpa_energy_density takes the (frequency, coarse point)
+ * entries of d already in the file from it and computes only the others, in blocks of one
+ * wave per lane; each block's entries are appended to the file (and flushed to the device)
+ * as soon as the block completes, so a run that stops -- a killed job, a failed node --
+ * loses at most the blocks in flight.  The file starts with a fingerprint of the problem
+ * (grid, V_loc, projectors, occupied states and eigenvalues, frequencies, coarse set, and
+ * the options that change d: lanczos_max, lanczos_rtol, stern_tol, stern_maxit, precision,
+ * reorth, fkind, refine, inner_tol, lanczos_block, refine_restart); a file written for
+ * another problem gives RPA_EINVAL and is left as it is.  A record cut short by a crash is
+ * dropped on resume.  An entry's status (RPA_ENOCONV, RPA_EBREAKDOWN) is that of its block
+ * and is reported again when the entry is resumed.  Contexts must not share a file.
+ * Supports the paper's full-cell runs, which take hours (Section 5). */
+rpa_status rpa_set_checkpoint(rpa_ctx *ctx, const char *path);
+
 /* E_c of several independent systems (contexts of possibly different grids, boundary
  * conditions, occupied sets and options) in one call: each context runs rpa_energy_density
  * on its own stream from its own host thread, so their kernels overlap on the GPU.

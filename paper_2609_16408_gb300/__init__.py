@@ -150,6 +150,7 @@ def _declare(lib):
         "rpa_tridiag_f11": ([I, I, P, P, I, P], I),
         "rpa_galerkin": ([P, I, P, P, P, I], I),
         "rpa_batch_energy": ([I, P, P, P], I),
+        "rpa_set_checkpoint": ([P, C.c_char_p], I),
         "rpa_galerkin_noalloc": ([LL, I, P, P, D, I, P, P, P, P], I),
         "rpa_status_string": ([I], C.c_char_p),
         "rpa_last_error": ([P], C.c_char_p),
@@ -323,6 +324,11 @@ def rpa_energy_density(ctx, nw, nprobe, nd, device_like=None, want_fine=True):
     _check(load().rpa_energy_density(ctx, _ptr(dco)[0], _ptr(dfi)[0] if dfi is not None else None,
                                      _ptr(ec)[0], C.byref(st), _where(dco, dfi, ec)), ctx)
     return dco, dfi, float(ec[0]), st.as_dict()
+
+
+def rpa_set_checkpoint(ctx, path):
+    """Checkpoint file of rpa_energy_density (None turns it off)."""
+    _check(load().rpa_set_checkpoint(ctx, os.fsencode(path) if path else None), ctx)
 
 
 def rpa_probe_density(ctx, probes, freqs, nl=None, want_tridiag=False, device_like=None,

@@ -19,6 +19,7 @@
 #include <thread>
 #include <vector>
 
+#include "checkpoint.cuh"
 #include "cocg.cuh"
 #include "cocg_fused.cuh"
 #include "small.cuh"
@@ -83,7 +84,10 @@ struct rpa_ctx {
   int interp_built = -1, stride_built[3] = {0, 0, 0};
   // wave workspace
   DevBuf Q, u64, v64, dens64, t64a, t64b, u32, t32a, t32b;
-  DevBuf x, r, p, p2, w, x64, r64, cdot, cpb, crb, part, sysd, sysi, gpart, cmat;
+  DevBuf x, r, p, p2, w, x64, cdot, cpb, crb, part, sysd, sysi, gpart, cmat;
+  // double-float (hi, lo) copies for the mixed form's refinement residual: V_loc, psi, the
+  // lo parts of the projector data, and u of the current wave
+  DevBuf vloc2, psi2, g_chi_lo, p_chi_lo, coef_lo, u2;
   // block Lanczos (options.lanczos_block > 1)
   DevBuf bD, bpart, bA, bB, bR, bRinv, bT, bW, blam, bsteps, bm, bfirst, bsize, bstart, bsz;
   DevBuf probe_d, pomega_d, active_d, steps_d, alpha_d, beta_d, lstate_d, coef_d, dots_d,
@@ -121,6 +125,8 @@ struct rpa_ctx {
   std::vector<int> hp_nnz, hp_nproj, hp_idx;
   std::vector<double> hp_chi, hp_gamma;
   double mem_share = 1.0;  // share of the free device memory a wave may take
+  std::vector<double> eps_h;  // occupied eigenvalues (host copy)
+  std::string ckpt_path;      // rpa_set_checkpoint: checkpoint file of rpa_energy_density
 };
 
 namespace rpa {
@@ -354,7 +360,8 @@ static int gram_chunks(long long nd) {
 static size_t per_probe_bytes(const rpa_ctx* c) {
   const long long nd = c->nd, ns = c->ns;
   size_t b = (size_t)ns * nd * cpx_bytes(c) * 4;
-  if (c->opt.precision != RPA_FP64 && c->opt.refine > 0) b += (size_t)ns * nd * 32;
+  if (c->opt.precision != RPA_FP64 && c->opt.refine > 0)
+    b += (size_t)ns * nd * sizeof(float4) + (size_t)nd * sizeof(float2);
   b += (size_t)(c->opt.lanczos_max + 1) * nd * 8 + (size_t)nd * 8 * 5 + (size_t)nd * 4 * 3;
   b += (size_t)ns * part_stride(c) * 4 * 8 + (size_t)ns * (kSysD * 8 + kSysI * 4);
   b += (size_t)ns * ns * (gram_chunks(nd) * 8 + 16);
@@ -391,8 +398,8 @@ static rpa_status ensure_workspace(rpa_ctx* c, int nb) {
     CK(c->t32a.ensure(sizeof(float) * nb * nd));
     CK(c->t32b.ensure(sizeof(float) * nb * nd));
     if (c->opt.refine > 0) {
-      CK(c->x64.ensure(sizeof(cpx<double>) * S * nd));
-      CK(c->r64.ensure(sizeof(cpx<double>) * S * nd));
+      CK(c->x64.ensure(sizeof(float4) * S * nd));  // double-float pairs
+      CK(c->u2.ensure(sizeof(float2) * nb * nd));
     }
   }
   CK(c->x.ensure(cb * S * nd));
@@ -840,14 +847,26 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
                               c->dens64.as<double>(), c->stream)));
     return RPA_OK;
   }
-  // FP64 refinement
-  cpx<double>*x64 = c->x64.as<cpx<double>>(), *r64 = c->r64.as<cpx<double>>();
+  // FP64 refinement.  The accumulated solution is kept as double-float pairs (hi, lo) of
+  // each component; the residual runs in double-float arithmetic on the FP32 units while
+  // the tolerance leaves room for its ~2^-48 rounding, else in FP64.
+  float4* x64 = c->x64.as<float4>();
+  cpx<double>* x64v = c->x64.as<cpx<double>>();  // the same storage, as the FP64 view's x
   const int all_but_idle = ((1 << kNumStatus) - 1) & ~(1 << kIdle);
-  CK((accumulate<double, float>(c->nd, S, c->sysi.as<int>(), all_but_idle, -1, x, x64, 1,
-                                c->stream)));
+  CK(accumulate_df(c->nd, S, c->sysi.as<int>(), all_but_idle, -1, x, x64, 1, c->stream));
   CK(convert_f2d(u32, c->u64.as<double>(), (long long)nb * c->nd, c->stream));
-  CocgView<double> cv64 = make_view<double>(c, nb, c->u64.as<double>(), x64, r64, nullptr,
+  CK(convert_d2df(c->u64.as<double>(), c->u2.as<float2>(), (long long)nb * c->nd, c->stream));
+  CocgView<double> cv64 = make_view<double>(c, nb, c->u64.as<double>(), x64v, nullptr, nullptr,
                                             nullptr);
+  DfAux aux;
+  aux.nl = nlview<float>(c);
+  aux.g_chi_lo = c->g_chi_lo.as<float>();
+  aux.p_chi_lo = c->p_chi_lo.as<float>();
+  aux.coef_lo = c->coef_lo.as<float>();
+  aux.vloc = c->vloc2.as<float2>();
+  aux.psi = c->psi2.as<float2>();
+  aux.u = c->u2.as<float2>();
+  const bool use_df = tol >= kDfResidualTol;
   // Each round replaces the FP32 recursive residual by the FP64 true residual.  By default
   // the FP32 recurrence then continues from its last direction (a reliable update: the
   // Krylov space built so far is kept) as long as a round reduces the residual by at most
@@ -859,12 +878,10 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
   bool rounds_left = false;  // the last round ran: its corrections are not checked yet
   for (int round = 1; round <= c->opt.refine; ++round) {
     rounds_left = false;
-    CK(proj_dots<double>(cv64.nl, c->nd, S, x64, cv64.sysi, 1 << kConverged, cv64.cdot,
-                         c->stream));
-    // double-float residual while its ~2^-48 rounding stays far below the tolerance
-    CK((cocg_resid<double, float>(cv64, x64, r64, nullptr, 1 << kConverged, r, p, x, c->stream,
-                                  tol >= kDfResidualTol,
-                                  cont ? c->p2.as<cpx<float>>() : nullptr)));
+    CK(proj_dots_df(aux, c->nd, S, x64, cv64.sysi, 1 << kConverged, cv64.cdot, c->stream));
+    CK((cocg_resid<double, float>(cv64, x64v, nullptr, nullptr, 1 << kConverged, r, p, x,
+                                  c->stream, use_df, cont ? c->p2.as<cpx<float>>() : nullptr,
+                                  &aux)));
     CK(cocg_scalars(S, cv64.tiles, cv64.part, cv64.sysd, cv64.sysi, cont ? 6 : 4,
                     1 << kConverged, tol, itol, maxit, 0, c->stream));
     int cnt[kNumStatus];
@@ -872,8 +889,7 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
     if (cnt[kActive] == 0) break;
     CKS(cocg_loop<float>(c, cv, maxit, cont));
     const int corrected = (1 << kConverged) | (1 << kMaxit) | (1 << kBreakdown);
-    CK((accumulate<double, float>(c->nd, S, c->sysi.as<int>(), corrected, round, x, x64, 0,
-                                  c->stream)));
+    CK(accumulate_df(c->nd, S, c->sysi.as<int>(), corrected, round, x, x64, 0, c->stream));
     // systems that were final before this round keep status kFinal and are skipped above;
     // systems corrected this round are kConverged again and are re-checked next round.
     rounds_left = true;
@@ -884,16 +900,15 @@ static rpa_status solve_mixed(rpa_ctx* c, int nb, const float* u32, const int* a
     int cnt[kNumStatus];
     CKS(counts(c, S, cnt));
     if (cnt[kConverged] > 0) {
-      CK(proj_dots<double>(cv64.nl, c->nd, S, x64, cv64.sysi, 1 << kConverged, cv64.cdot,
-                           c->stream));
-      CK((cocg_resid<double, float>(cv64, x64, r64, nullptr, 1 << kConverged, nullptr, nullptr,
-                                    nullptr, c->stream, tol >= kDfResidualTol)));
+      CK(proj_dots_df(aux, c->nd, S, x64, cv64.sysi, 1 << kConverged, cv64.cdot, c->stream));
+      CK((cocg_resid<double, float>(cv64, x64v, nullptr, nullptr, 1 << kConverged, nullptr,
+                                    nullptr, nullptr, c->stream, use_df, nullptr, &aux)));
       CK(cocg_scalars(S, cv64.tiles, cv64.part, cv64.sysd, cv64.sysi, 7, 1 << kConverged, tol,
                       itol, maxit, 0, c->stream));
     }
   }
   CKS(collect_stats(c, S, ss));
-  CK((density<double, double>(c->nd, c->ns, nb, c->d64.psi.as<double>(), x64, active,
+  CK((density_df(c->nd, c->ns, nb, c->d64.psi.as<double>(), x64, active,
                               c->dens64.as<double>(), c->stream)));
   return RPA_OK;
 }
@@ -1549,6 +1564,8 @@ rpa_status rpa_set_potential(rpa_ctx* c, const double* vloc, int where) {
   CK(c->d32.vloc.ensure(sizeof(float) * c->nd));
   CKS(copy_in(c, c->d64.vloc.p, vloc, sizeof(double) * c->nd, where));
   CK(convert_d2f(c->d64.vloc.as<double>(), c->d32.vloc.as<float>(), c->nd, c->stream));
+  CK(c->vloc2.ensure(sizeof(float2) * c->nd));
+  CK(convert_d2df(c->d64.vloc.as<double>(), c->vloc2.as<float2>(), c->nd, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->have_vloc = true;
   drop_lanes(c);
@@ -1640,6 +1657,14 @@ rpa_status rpa_set_projectors(rpa_ctx* c, int ngroups, const int* nnz, const int
   CK(cudaMemcpy(c->tile_ranges.p, trng.data(), sizeof(int) * trng.size(), cudaMemcpyHostToDevice));
   std::vector<float> gchi_f(gchi.begin(), gchi.end()), gcoef_f(gcoef.begin(), gcoef.end()),
       pchi_f(pchi.begin(), pchi.end());
+  // lo parts of the double-float pairs (hi = the FP32 copy)
+  auto lo_of = [](const std::vector<double>& v, const std::vector<float>& h) {
+    std::vector<float> lo(v.size());
+    for (size_t i = 0; i < v.size(); ++i) lo[i] = (float)(v[i] - (double)h[i]);
+    return lo;
+  };
+  const std::vector<float> gchi_lo = lo_of(gchi, gchi_f), pchi_lo = lo_of(pchi, pchi_f),
+                           gcoef_lo = lo_of(gcoef, gcoef_f);
   const size_t Eb = std::max<long long>(E, 1);
   CK(c->g_off.ensure(sizeof(int) * goff.size()));
   CK(c->g_idx.ensure(sizeof(int) * Eb));
@@ -1651,6 +1676,9 @@ rpa_status rpa_set_projectors(rpa_ctx* c, int ngroups, const int* nnz, const int
   CK(c->d32.p_chi.ensure(sizeof(float) * Eb * kProjChunk));
   CK(c->d64.coef.ensure(sizeof(double) * std::max(NG, 1) * kProjChunk));
   CK(c->d32.coef.ensure(sizeof(float) * std::max(NG, 1) * kProjChunk));
+  CK(c->g_chi_lo.ensure(sizeof(float) * Eb * kProjChunk));
+  CK(c->p_chi_lo.ensure(sizeof(float) * Eb * kProjChunk));
+  CK(c->coef_lo.ensure(sizeof(float) * std::max(NG, 1) * kProjChunk));
   CK(cudaMemcpy(c->g_off.p, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->p_off.p, poff.data(), sizeof(int) * (nd + 1), cudaMemcpyHostToDevice));
   if (E > 0) {
@@ -1662,6 +1690,9 @@ rpa_status rpa_set_projectors(rpa_ctx* c, int ngroups, const int* nnz, const int
     CK(cudaMemcpy(c->d32.p_chi.p, pchi_f.data(), sizeof(float) * E * kProjChunk, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d64.coef.p, gcoef.data(), sizeof(double) * NG * kProjChunk, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d32.coef.p, gcoef_f.data(), sizeof(float) * NG * kProjChunk, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->g_chi_lo.p, gchi_lo.data(), sizeof(float) * E * kProjChunk, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->p_chi_lo.p, pchi_lo.data(), sizeof(float) * E * kProjChunk, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->coef_lo.p, gcoef_lo.data(), sizeof(float) * NG * kProjChunk, cudaMemcpyHostToDevice));
   }
   c->ngroup = NG;
   // host copy of the inputs, for lane contexts
@@ -1698,8 +1729,11 @@ rpa_status rpa_set_occupied(rpa_ctx* c, int ns, const double* psi, const double*
   CK(c->eps_d.ensure(sizeof(double) * ns));
   CKS(copy_in(c, c->d64.psi.p, psi, sizeof(double) * n, where));
   CK(convert_d2f(c->d64.psi.as<double>(), c->d32.psi.as<float>(), n, c->stream));
+  CK(c->psi2.ensure(sizeof(float2) * n));
+  CK(convert_d2df(c->d64.psi.as<double>(), c->psi2.as<float2>(), n, c->stream));
   CK(cudaMemcpyAsync(c->eps_d.p, e.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  c->eps_h = e;
   c->ns = ns;
   c->have_occ = true;
   c->ws_nb = 0;
@@ -1888,12 +1922,58 @@ rpa_status rpa_interpolate(rpa_ctx* c, const double* d_coarse, double* d_fine, d
   return RPA_OK;
 }
 
+// Fingerprint of everything that fixes d on C_g: grid, inputs (V_loc, projectors, occupied
+// states and eigenvalues), frequencies, the coarse set and the options that change d.
+static rpa_status problem_key(rpa_ctx* c, const std::vector<long long>& idx,
+                              unsigned long long* key) {
+  unsigned long long h = kFnvBasis;
+  auto mix = [&h](const void* p, size_t n) { h = fnv1a(h, p, n); };
+  auto mixv = [&mix](const auto& v) {
+    const long long n = (long long)v.size();
+    mix(&n, sizeof(n));
+    if (n) mix(v.data(), sizeof(v[0]) * v.size());
+  };
+  const rpa_grid& g = c->grid;
+  mix(g.n, sizeof(g.n));
+  mix(g.h, sizeof(g.h));
+  mix(g.bc, sizeof(g.bc));
+  mix(&g.fd_radius, sizeof(g.fd_radius));
+  std::vector<double> hv((size_t)c->nd);
+  CK(cudaMemcpy(hv.data(), c->d64.vloc.p, sizeof(double) * c->nd, cudaMemcpyDeviceToHost));
+  mixv(hv);
+  hv.resize((size_t)c->ns * c->nd);
+  CK(cudaMemcpy(hv.data(), c->d64.psi.p, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost));
+  mixv(hv);
+  mixv(c->eps_h);
+  mix(&c->hp_ng, sizeof(c->hp_ng));
+  mixv(c->hp_nnz);
+  mixv(c->hp_nproj);
+  mixv(c->hp_idx);
+  mixv(c->hp_chi);
+  mixv(c->hp_gamma);
+  mixv(c->omega);
+  mixv(idx);
+  const rpa_options& o = c->opt;
+  const double dopt[] = {o.lanczos_rtol, o.stern_tol, o.inner_tol};
+  const int iopt[] = {o.lanczos_max, o.stern_maxit, o.precision, o.reorth,  o.fkind,
+                      o.refine,      o.lanczos_block, o.refine_restart};
+  mix(dopt, sizeof(dopt));
+  mix(iopt, sizeof(iopt));
+  *key = h;
+  return RPA_OK;
+}
+
+rpa_status rpa_set_checkpoint(rpa_ctx* c, const char* path) {
+  if (!c) return RPA_EINVAL;
+  c->ckpt_path = path ? path : "";
+  return RPA_OK;
+}
+
 rpa_status rpa_energy_density(rpa_ctx* c, double* d_coarse, double* d_fine, double* ec,
                               rpa_stats* st, int where) {
   CKS(check_ready(c, true));
   auto t0 = std::chrono::steady_clock::now();
   if (st) std::memset(st, 0, sizeof(*st));
-  c->prof_stats = st;
   const long long P = num_probes(c);
   std::vector<long long> idx(P);
   CKS(rpa_probe_indices(c, idx.data()));
@@ -1906,10 +1986,67 @@ rpa_status rpa_energy_density(rpa_ctx* c, double* d_coarse, double* d_fine, doub
       om[k * P + j] = c->omega[k];
     }
   c->soft = RPA_OK;
-  rpa_status rs = run_probes_lanes(c, count, pr.data(), om.data(), dh.data(), nullptr, nullptr,
-                                   nullptr, st);
-  c->prof_stats = nullptr;
-  CKS(rs);
+  c->soft_msg.clear();
+  if (c->ckpt_path.empty()) {
+    c->prof_stats = st;
+    rpa_status rs = run_probes_lanes(c, count, pr.data(), om.data(), dh.data(), nullptr,
+                                     nullptr, nullptr, st);
+    c->prof_stats = nullptr;
+    CKS(rs);
+  } else {
+    // resume: entries in the checkpoint are taken from it; the others run in blocks of one
+    // wave per lane, each block's entries appended to the file when the block completes
+    unsigned long long key = 0;
+    CKS(problem_key(c, idx, &key));
+    Checkpoint ck;
+    std::vector<CkptRecord> recs;
+    std::string msg;
+    if (ck.open(c->ckpt_path, key, count, &recs, &msg) != RPA_OK) return fail(c, RPA_EINVAL, msg);
+    std::vector<char> done(count, 0);
+    for (const CkptRecord& r : recs) {
+      dh[r.entry] = r.d;
+      done[r.entry] = 1;
+      if (r.status == RPA_ENOCONV || r.status == RPA_EBREAKDOWN)
+        note_soft(c, (rpa_status)r.status, "a solve of an entry resumed from the checkpoint");
+    }
+    std::vector<long long> todo;
+    for (long long i = 0; i < count; ++i)
+      if (!done[i]) todo.push_back(i);
+    const long long block =
+        (long long)choose_batch(c, (long long)todo.size()) * std::max(1, c->opt.lanes);
+    std::vector<long long> bpr;
+    std::vector<double> bom, bd;
+    for (size_t b0 = 0; b0 < todo.size(); b0 += (size_t)block) {
+      const size_t n = std::min(todo.size() - b0, (size_t)block);
+      bpr.resize(n);
+      bom.resize(n);
+      bd.assign(n, 0.0);
+      for (size_t i = 0; i < n; ++i) {
+        bpr[i] = pr[todo[b0 + i]];
+        bom[i] = om[todo[b0 + i]];
+      }
+      const rpa_status prev = c->soft;
+      const std::string prev_msg = c->soft_msg;
+      c->soft = RPA_OK;
+      c->prof_stats = st;
+      rpa_status rs = run_probes_lanes(c, (long long)n, bpr.data(), bom.data(), bd.data(),
+                                       nullptr, nullptr, nullptr, st);
+      c->prof_stats = nullptr;
+      const rpa_status bs = c->soft;
+      const std::string bmsg = c->soft_msg;
+      c->soft = prev;
+      c->soft_msg = prev_msg;
+      if (bs != RPA_OK) note_soft(c, bs, bmsg.c_str());
+      CKS(rs);
+      recs.resize(n);
+      for (size_t i = 0; i < n; ++i) {
+        const long long e = todo[b0 + i];
+        dh[e] = bd[i];
+        recs[i] = CkptRecord{e, bd[i], (int)bs, 0u};
+      }
+      if (ck.append(recs, &msg) != RPA_OK) return fail(c, RPA_EINVAL, msg);
+    }
+  }
   auto t1 = std::chrono::steady_clock::now();
   DevBuf dco, dfi, ecd;
   CK(dco.ensure(sizeof(double) * count));

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "cocg.cuh"
+#include "fused_dev.cuh"
 
 namespace rpa {
 
@@ -385,6 +386,97 @@ __global__ void __launch_bounds__(256) k_density(long long nd, int ns, int nb,
 }
 
 // -------------------------------------------------------------------------------------------
+// double-float form of the mixed form's FP64 solution (float4 per complex value:
+// re.hi, re.lo, im.hi, im.lo)
+// -------------------------------------------------------------------------------------------
+__global__ void k_d2df(const double* __restrict__ a, float2* __restrict__ b, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = a[i];
+    const float h = __double2float_rn(v);
+    b[i] = make_float2(h, __double2float_rn(v - (double)h));
+  }
+}
+
+__global__ void k_accumulate_df(long long nd, const int* __restrict__ sysi, int mask, int round,
+                                const cpx<float>* __restrict__ xl, float4* __restrict__ xh,
+                                int set) {
+  const int s = blockIdx.y;
+  if (!((mask >> sysi[(long long)s * kSysI + kStatus]) & 1)) return;
+  if (round >= 0 && sysi[(long long)s * kSysI + kRestarts] != round) return;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nd;
+       p += (long long)gridDim.x * blockDim.x) {
+    const long long q = (long long)s * nd + p;
+    const cpx<float> a = xl[q];
+    if (set) {
+      xh[q] = make_float4(a.re, 0.f, a.im, 0.f);
+    } else {
+      const float4 v = xh[q];
+      const df re = df_add(df{v.x, v.y}, df{a.re, 0.f}), im = df_add(df{v.z, v.w}, df{a.im, 0.f});
+      xh[q] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_density_df(long long nd, int ns, int nb,
+                                                    const double* __restrict__ psi,
+                                                    const float4* __restrict__ x,
+                                                    const int* __restrict__ probe_active,
+                                                    double* __restrict__ dens) {
+  const int b = blockIdx.y;
+  if (probe_active && !probe_active[b]) return;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nd;
+       p += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int n = 0; n < ns; ++n) {
+      const float4 v = x[((long long)b * ns + n) * nd + p];
+      acc += psi[(long long)n * nd + p] * ((double)v.x + (double)v.y);
+    }
+    dens[(long long)b * nd + p] = 4.0 * acc;
+  }
+}
+
+// cd[s][g][l] = gamma dV sum_e chi(e) x_s(idx_e) with double-float products and sums; the
+// block's partial sums are combined in double-float through shared memory
+__global__ void __launch_bounds__(128) k_proj_dots_df(DfAux aux, long long nd,
+                                                      const float4* __restrict__ vec,
+                                                      const int* __restrict__ sysi, int mask,
+                                                      cpx<double>* __restrict__ cd) {
+  const int g = blockIdx.x, s = blockIdx.y;
+  if (sysi && !selected(sysi, s, mask)) return;
+  __shared__ df sh[128 * 2 * kProjChunk];
+  const float4* v = vec + (long long)s * nd;
+  df acc[2 * kProjChunk];
+#pragma unroll
+  for (int q = 0; q < 2 * kProjChunk; ++q) acc[q] = df{0.f, 0.f};
+  for (int e = aux.nl.g_off[g] + threadIdx.x; e < aux.nl.g_off[g + 1]; e += blockDim.x) {
+    const float4 xv = v[aux.nl.g_idx[e]];
+#pragma unroll
+    for (int l = 0; l < kProjChunk; ++l) {
+      const df ch{aux.nl.g_chi[(long long)e * kProjChunk + l], aux.g_chi_lo[(long long)e * kProjChunk + l]};
+      acc[2 * l] = df_fma(acc[2 * l], ch, df{xv.x, xv.y});
+      acc[2 * l + 1] = df_fma(acc[2 * l + 1], ch, df{xv.z, xv.w});
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2 * kProjChunk; ++q) sh[q * 128 + threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < 2 * kProjChunk; ++q)
+        sh[q * 128 + threadIdx.x] = df_add(sh[q * 128 + threadIdx.x], sh[q * 128 + threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x < kProjChunk) {
+    const int l = threadIdx.x;
+    const df cf{aux.nl.coef[g * kProjChunk + l], aux.coef_lo[g * kProjChunk + l]};
+    const df re = df_mul(cf, sh[(2 * l) * 128]), im = df_mul(cf, sh[(2 * l + 1) * 128]);
+    cd[((long long)s * aux.nl.ngroup + g) * kProjChunk + l] = mk<double>(df_val(re), df_val(im));
+  }
+}
+
+// -------------------------------------------------------------------------------------------
 // launchers
 // -------------------------------------------------------------------------------------------
 template <typename T>
@@ -453,6 +545,39 @@ cudaError_t density(long long nd, int ns, int nb, const TP* psi, const cpx<TX>* 
                     const int* probe_active, double* dens, cudaStream_t s) {
   dim3 grid((unsigned)std::min<long long>((nd + 255) / 256, 256), nb);
   k_density<TX, TP><<<grid, 256, 0, s>>>(nd, ns, nb, psi, x, probe_active, dens);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t convert_d2df(const double* a, float2* b, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_d2df<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(a, b, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t accumulate_df(long long nd, int nsys, const int* sysi, int mask, int round,
+                          const cpx<float>* xl, float4* xh, int set, cudaStream_t s) {
+  if (nsys <= 0) return cudaSuccess;
+  dim3 grid((unsigned)std::min<long long>((nd + 255) / 256, 256), nsys);
+  k_accumulate_df<<<grid, 256, 0, s>>>(nd, sysi, mask, round, xl, xh, set);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t density_df(long long nd, int ns, int nb, const double* psi, const float4* x,
+                       const int* probe_active, double* dens, cudaStream_t s) {
+  dim3 grid((unsigned)std::min<long long>((nd + 255) / 256, 256), nb);
+  k_density_df<<<grid, 256, 0, s>>>(nd, ns, nb, psi, x, probe_active, dens);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t proj_dots_df(const DfAux& aux, long long nd, int nsys, const float4* x,
+                         const int* sysi, int mask, cpx<double>* cd, cudaStream_t s) {
+  if (aux.nl.ngroup == 0 || nsys == 0) return cudaSuccess;
+  dim3 grid(aux.nl.ngroup, nsys);
+  k_proj_dots_df<<<grid, 128, 0, s>>>(aux, nd, x, sysi, mask, cd);
   note_launch();
   return cudaGetLastError();
 }

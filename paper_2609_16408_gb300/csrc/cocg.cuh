@@ -46,15 +46,45 @@ template <typename T>
 cudaError_t apply_h(const Stencil<T>& st, const T* vloc, const NonlocalDev<T>& nl, long long nd,
                     int count, const cpx<T>* x, const cpx<T>* sigma, cpx<T>* cd, cpx<T>* y,
                     cudaStream_t s);
+// Double-float form of the mixed form's FP64 quantities (each value an unevaluated sum
+// hi + lo of two floats, about 48 significant bits), so that the refinement residual runs
+// on the FP32 units: the hi parts of the projector data are the FP32 copies.
+struct DfAux {
+  NonlocalDev<float> nl;    // hi parts: g_chi, p_chi, coef
+  const float* g_chi_lo;    // lo parts of the group-major projector values
+  const float* p_chi_lo;    // lo parts of the point-major projector values
+  const float* coef_lo;     // lo parts of gamma dV
+  const float2* vloc;       // (hi, lo) of V_loc, N_d
+  const float2* psi;        // (hi, lo) of psi, ns x N_d
+  const float2* u;          // (hi, lo) of u, per probe slot x N_d
+};
+// (hi, lo) pairs of a double array
+cudaError_t convert_d2df(const double* a, float2* b, long long n, cudaStream_t s);
+// mixed-form FP64 solution kept as double-float pairs (re.hi, re.lo, im.hi, im.lo):
+// xh = xl (set) or xh += xl for the selected systems (as accumulate)
+cudaError_t accumulate_df(long long nd, int nsys, const int* sysi, int mask, int round,
+                          const cpx<float>* xl, float4* xh, int set, cudaStream_t s);
+// dens_b = 4 sum_n psi_n (.) Re x_{b,n} from double-float x (FP64 sums)
+cudaError_t density_df(long long nd, int ns, int nb, const double* psi, const float4* x,
+                       const int* probe_active, double* dens, cudaStream_t s);
+// projector coefficients gamma dV chi^T x of double-float x, in double-float sums, as FP64
+cudaError_t proj_dots_df(const DfAux& aux, long long nd, int nsys, const float4* x,
+                         const int* sysi, int mask, cpx<double>* cd, cudaStream_t s);
+
 // With r_lo: the low-precision copy r_lo = r, x_lo = 0, and p_lo = r_lo (restart) -- or, with
 // p_keep, the direction of the previous loop is kept for a continued recurrence: it is
 // copied from p_keep into p_lo for systems whose last loop ran an odd number of iterations
 // (their latest direction is in the other buffer of the pair), and p_lo = r_lo only for
 // systems that did not iterate.
+// For T = double, TL = float (the mixed form's refinement) x holds double-float pairs
+// (float4 per complex value, see accumulate_df), r may be null (the FP64 residual is then
+// not stored), and use_df needs aux: the whole residual then runs in double-float
+// arithmetic; without use_df x is converted to FP64 as it is loaded.
 template <typename T, typename TL>
 cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
                        cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s,
-                       bool use_df = false, const cpx<TL>* p_keep = nullptr);
+                       bool use_df = false, const cpx<TL>* p_keep = nullptr,
+                       const DfAux* aux = nullptr);
 // Per-system scalar step (kind: 0 init, 1 alpha, 2 beta/convergence, 3 true-residual
 // recheck, 4 FP64 refinement check (restart), 5 mixed-form init, 6 FP64 refinement check
 // continuing the recurrence: beta = rho(new true residual) / rho(last recursive step),

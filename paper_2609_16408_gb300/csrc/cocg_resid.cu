@@ -27,57 +27,26 @@ namespace {
 
 constexpr int kRTX = 32, kRTY = 8;
 
-// ---- double-float arithmetic -----------------------------------------------------------
-struct df {
-  float hi, lo;
-};
-__device__ __forceinline__ df df_of(double x) {
-  const float h = __double2float_rn(x);
-  return df{h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ double df_val(df a) { return (double)a.hi + (double)a.lo; }
-// s + e = a + b exactly (Knuth's two-sum)
-__device__ __forceinline__ df two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return df{s, (a - (s - bb)) + (b - bb)};
-}
-// s + e = a + b exactly, |a| >= |b|
-__device__ __forceinline__ df fast_two_sum(float a, float b) {
-  const float s = a + b;
-  return df{s, b - (s - a)};
-}
-__device__ __forceinline__ df df_add(df a, df b) {
-  const df s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
-}
-// acc + c * x with the product formed exactly in hi (Dekker's product through FMA)
-__device__ __forceinline__ df df_fma(df acc, df c, df x) {
-  const float p = c.hi * x.hi;
-  float e = fmaf(c.hi, x.hi, -p);
-  e = fmaf(c.hi, x.lo, fmaf(c.lo, x.hi, e));
-  const df s = two_sum(acc.hi, p);
-  return fast_two_sum(s.hi, s.lo + (acc.lo + e));
-}
-struct cdf {
-  df re, im;
-};
-__device__ __forceinline__ cdf cdf_of(const cpx<double>& v) { return cdf{df_of(v.re), df_of(v.im)}; }
-
-// the 6R-neighbour coefficients as double-float pairs (kernel parameters)
+// the stencil coefficients as double-float pairs (kernel parameters)
 struct DfCoef {
   float hx[kMaxRadius + 1], lx[kMaxRadius + 1], hy[kMaxRadius + 1], ly[kMaxRadius + 1],
       hz[kMaxRadius + 1], lz[kMaxRadius + 1];
+  float c0h, c0l;
 };
 
-// DF: FP64 data, 6R-neighbour sum in double-float (see the file comment)
+// XDF (T = double, TL = float: the mixed form's refinement): x holds double-float pairs.
+// DF (with XDF): the whole residual in double-float arithmetic on the FP32 units; without
+// DF the loaded pairs are summed into FP64 and the FP64 arithmetic follows.
 template <typename T, typename TL, int R, bool SMEM_CD, bool DF>
 __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
     k_resid_fused(CocgView<T> cv, const cpx<T>* __restrict__ x, cpx<T>* __restrict__ r,
                   cpx<T>* __restrict__ pdir, int mask, cpx<TL>* __restrict__ r_lo,
                   cpx<TL>* __restrict__ p_lo, cpx<TL>* __restrict__ x_lo, int zchunk,
-                  DfCoef dc, const cpx<TL>* __restrict__ p_keep) {
+                  DfCoef dc, const cpx<TL>* __restrict__ p_keep, DfAux aux) {
+  constexpr bool XDF = sizeof(T) == 8 && std::is_same<TL, float>::value;
+  static_assert(!DF || XDF, "the double-float path is the mixed form's refinement");
   using V = typename std::conditional<DF, cdf, cpx<T>>::type;  // stored neighbour values
+  using AT = typename std::conditional<DF, float, T>::type;    // partial sums
   const int s = blockIdx.y;
   const int st_s = cv.sysi[(long long)s * kSysI + kStatus];
   if (!((mask >> st_s) & 1)) return;
@@ -93,7 +62,7 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
   constexpr int NHALO = PLN - kRTX * kRTY;
   constexpr int HPT = (NHALO + kRTX * kRTY - 1) / (kRTX * kRTY);
   __shared__ V pl[2 * PLN];
-  __shared__ T sh[8 * 4];
+  __shared__ AT sh[8 * 4];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   const Stencil<T>& st = cv.st;
   const int nx = st.nx, ny = st.ny, nz = st.nz;
@@ -106,6 +75,7 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
   const bool valid = gx < nx && gy < ny;
   const long long sbase = (long long)s * cv.nd;
   const cpx<T>* __restrict__ xs = x + sbase;
+  const float4* __restrict__ xd = reinterpret_cast<const float4*>(x) + sbase;  // XDF
   const T* __restrict__ vloc = cv.vloc;
   const int b = s / cv.ns, n = s - b * cv.ns;
   const cpx<T> sigma = mk<T>((T)cv.eps[n], (T)cv.omega[b]);
@@ -113,10 +83,17 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
   const T* __restrict__ ub = cv.u + (long long)b * cv.nd;
   const int ncd = cv.nl.ngroup * kProjChunk;
   const cpx<T>* cd = cv.cdot + (long long)s * ncd;
+  const cdf* cdd = nullptr;  // DF: the coefficients as double-float pairs in shared memory
   if (SMEM_CD) {
-    cpx<T>* scd = reinterpret_cast<cpx<T>*>(dyn_smem);
-    for (int i = threadIdx.x; i < ncd; i += blockDim.x) scd[i] = cd[i];
-    cd = scd;  // read after the first barrier of the z loop
+    if constexpr (DF) {
+      cdf* scd = reinterpret_cast<cdf*>(dyn_smem);
+      for (int i = threadIdx.x; i < ncd; i += blockDim.x) scd[i] = cdf_of(cd[i]);
+      cdd = scd;
+    } else {
+      cpx<T>* scd = reinterpret_cast<cpx<T>*>(dyn_smem);
+      for (int i = threadIdx.x; i < ncd; i += blockDim.x) scd[i] = cd[i];
+      cd = scd;  // read after the first barrier of the z loop
+    }
   }
   // partial slots past this launch's tiles: zeroed by the first block of the system
   if (blockIdx.x == 0 && blockIdx.z == 0) {
@@ -164,7 +141,11 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
   };
   auto ld = [&](int q) -> V {
     if constexpr (DF) {
-      return q < 0 ? cdf{df{0.f, 0.f}, df{0.f, 0.f}} : cdf_of(xs[q]);
+      return q < 0 ? cdf{df{0.f, 0.f}, df{0.f, 0.f}} : cdf_ld(xd[q]);
+    } else if constexpr (XDF) {
+      if (q < 0) return mk<T>((T)0, (T)0);
+      const cdf v = cdf_ld(xd[q]);
+      return mk<T>(df_val(v.re), df_val(v.im));
     } else {
       return q < 0 ? mk<T>((T)0, (T)0) : xs[q];
     }
@@ -194,8 +175,10 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
     }
   };
   if (z0 < z1) prefetch(z0);
-  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  AT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
   const T c0 = st.c0;
+  // DF: sigma = eps_n + i omega_b as double-float pairs
+  const df smr = df_of(-(double)cv.eps[n]), smi = df_of((double)cv.omega[b]);
   for (int z = z0; z < z1; ++z) {
     const int bo = ((z - z0) & 1) * PLN;
     zq[2 * R] = nq;
@@ -209,10 +192,10 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
     if (valid) {
       const int q = own_xy + z * plane;
       const V* cs = pl + bo + own_slot;
-      const T dg = c0 + vloc[q];
-      cpx<T> c, a;
       if constexpr (DF) {
-        c = mk<T>(df_val(zq[R].re), df_val(zq[R].im));
+        // (H - sigma) x at q: neighbours, diagonal (c0 + V - sigma), projector terms and
+        // b = -psi_n u, every product and sum in double-float arithmetic
+        const cdf c = zq[R];
         df sr{0.f, 0.f}, si{0.f, 0.f};
 #pragma unroll
         for (int m = 1; m <= R; ++m) {
@@ -224,18 +207,51 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
           sr = df_fma(sr, kz, df_add(zq[R - m].re, zq[R + m].re));
           si = df_fma(si, kz, df_add(zq[R - m].im, zq[R + m].im));
         }
-        a = mk<T>(df_val(sr) + (dg * c.re - (sigma.re * c.re - sigma.im * c.im)),
-                  df_val(si) + (dg * c.im - (sigma.re * c.im + sigma.im * c.re)));
-      } else {
-        c = zq[R];
-        a = mk<T>(dg * c.re - (sigma.re * c.re - sigma.im * c.im),
-                  dg * c.im - (sigma.re * c.im + sigma.im * c.re));
+        const float2 vq = aux.vloc[q];
+        const df dd = df_add(df_add(df{dc.c0h, dc.c0l}, df{vq.x, vq.y}), smr);  // c0 + V - Re sigma
+        df are = df_add(df_fma(df_mul(dd, c.re), smi, c.im), sr);
+        df aim = df_add(df_fma(df_mul(dd, c.im), df_neg(smi), c.re), si);
+        for (int e = e0; e < e1; ++e) {
+          const int g = p_grp[e];
+          const cdf* cg = cdd ? cdd + kProjChunk * g : nullptr;
 #pragma unroll
-        for (int m = 1; m <= R; ++m) {
-          a = caxpy_r(a, st.cx[m], cadd(cs[-m], cs[m]));
-          a = caxpy_r(a, st.cy[m], cadd(cs[-m * EXN], cs[m * EXN]));
-          a = caxpy_r(a, st.cz[m], cadd(zq[R - m], zq[R + m]));
+          for (int l = 0; l < kProjChunk; ++l) {
+            const df ch{aux.nl.p_chi[kProjChunk * e + l], aux.p_chi_lo[kProjChunk * e + l]};
+            const cdf cl = cg ? cg[l] : cdf_of(cd[kProjChunk * g + l]);
+            are = df_fma(are, ch, cl.re);
+            aim = df_fma(aim, ch, cl.im);
+          }
         }
+        const float2 pq = aux.psi[(long long)n * cv.nd + q], uq = aux.u[(long long)b * cv.nd + q];
+        const df bre = df_neg(df_mul(df{pq.x, pq.y}, df{uq.x, uq.y}));
+        const df rre = df_add(bre, df_neg(are)), rim = df_neg(aim);
+        const float rr = __fadd_rn(rre.hi, rre.lo), ri = __fadd_rn(rim.hi, rim.lo);
+        if (r) r[sbase + q] = mk<T>((T)df_val(rre), (T)df_val(rim));
+        if (r_lo) {
+          const cpx<TL> rl = mk<TL>((TL)rr, (TL)ri);
+          r_lo[sbase + q] = rl;
+          if (pmode == 0)
+            p_lo[sbase + q] = rl;
+          else if (pmode == 2)
+            p_lo[sbase + q] = p_keep[sbase + q];
+          x_lo[sbase + q] = mk<TL>((TL)0, (TL)0);
+        }
+        const float bv = __fadd_rn(bre.hi, bre.lo);
+        a0 += rr * rr + ri * ri;
+        a1 += bv * bv;
+        a2 += rr * rr - ri * ri;
+        a3 += 2.f * rr * ri;
+      } else {
+      const T dg = c0 + vloc[q];
+      cpx<T> c, a;
+      c = zq[R];
+      a = mk<T>(dg * c.re - (sigma.re * c.re - sigma.im * c.im),
+                dg * c.im - (sigma.re * c.im + sigma.im * c.re));
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        a = caxpy_r(a, st.cx[m], cadd(cs[-m], cs[m]));
+        a = caxpy_r(a, st.cy[m], cadd(cs[-m * EXN], cs[m * EXN]));
+        a = caxpy_r(a, st.cz[m], cadd(zq[R - m], zq[R + m]));
       }
       for (int e = e0; e < e1; ++e) {
         const int g = p_grp[e];
@@ -247,7 +263,7 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
       }
       const cpx<T> bv = mk<T>(-psin[q] * ub[q], (T)0);
       const cpx<T> rv = csub(bv, a);
-      r[sbase + q] = rv;
+      if (r) r[sbase + q] = rv;
       if (pdir) pdir[sbase + q] = rv;
       if (r_lo) {
         const cpx<TL> rl = mk<TL>((TL)rv.re, (TL)rv.im);
@@ -262,12 +278,13 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
       a1 += bv.re * bv.re;
       a2 += rv.re * rv.re - rv.im * rv.im;
       a3 += (T)2 * rv.re * rv.im;
+      }
     }
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) zq[i] = zq[i + 1];
   }
-  T acc[4] = {a0, a1, a2, a3};
-  block_sum_t<T, 4>(acc, sh);
+  AT acc[4] = {a0, a1, a2, a3};
+  block_sum_t<AT, 4>(acc, sh);
   if (threadIdx.x == 0) {
     const int pid = blockIdx.x + gridDim.x * blockIdx.z;
     double* pp = cv.part + ((long long)s * cv.tiles + pid) * 4;
@@ -279,7 +296,7 @@ __global__ void __launch_bounds__(kRTX * kRTY, sizeof(T) == 4 ? 3 : 2)
 template <typename T, typename TL, int R>
 void launch_r(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
               cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, bool use_df,
-              const cpx<TL>* p_keep, cudaStream_t s) {
+              const cpx<TL>* p_keep, const DfAux& aux, cudaStream_t s) {
   constexpr size_t kPlanes = 2 * sizeof(cpx<T>) * (kRTX + 2 * R) * (kRTY + 2 * R);
   size_t cdb = sizeof(cpx<T>) * cv.nl.ngroup * kProjChunk;
   if (cdb + kPlanes + 1024 > 48 * 1024) cdb = 0;
@@ -298,24 +315,26 @@ void launch_r(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, i
         lo[a][m] = (float)(v[a] - (double)hi[a][m]);
       }
     }
+    dc.c0h = (float)(double)cv.st.c0;
+    dc.c0l = (float)((double)cv.st.c0 - (double)dc.c0h);
   }
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (sizeof(T) == 8 && std::is_same<TL, float>::value) {
     if (use_df) {
       if (cdb)
         k_resid_fused<T, TL, R, true, true><<<grid, kRTX * kRTY, cdb, s>>>(
-            cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc, p_keep);
+            cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc, p_keep, aux);
       else
         k_resid_fused<T, TL, R, false, true><<<grid, kRTX * kRTY, 0, s>>>(
-            cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc, p_keep);
+            cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc, p_keep, aux);
       return;
     }
   }
   if (cdb)
     k_resid_fused<T, TL, R, true, false><<<grid, kRTX * kRTY, cdb, s>>>(
-        cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc, p_keep);
+        cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc, p_keep, aux);
   else
     k_resid_fused<T, TL, R, false, false><<<grid, kRTX * kRTY, 0, s>>>(
-        cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc, p_keep);
+        cv, x, r, pdir, mask, r_lo, p_lo, x_lo, zchunk, dc, p_keep, aux);
 }
 
 }  // namespace
@@ -323,22 +342,27 @@ void launch_r(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, i
 template <typename T, typename TL>
 cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>* pdir, int mask,
                        cpx<TL>* r_lo, cpx<TL>* p_lo, cpx<TL>* x_lo, cudaStream_t s,
-                       bool use_df, const cpx<TL>* p_keep) {
+                       bool use_df, const cpx<TL>* p_keep, const DfAux* aux) {
   if (p_keep && !r_lo) return cudaErrorInvalidValue;
+  constexpr bool kXdf = sizeof(T) == 8 && std::is_same<TL, float>::value;
+  if (use_df && (!kXdf || !aux)) return cudaErrorInvalidValue;
+  if (!kXdf && !r) return cudaErrorInvalidValue;
+  const DfAux noaux{};
+  const DfAux& ax = aux ? *aux : noaux;
   const int nx = cv.st.nx, ny = cv.st.ny, nz = cv.st.nz;
   const int zchunk = nz <= 64 ? nz : 32;
   const long long used = (long long)((nx + kRTX - 1) / kRTX) * ((ny + kRTY - 1) / kRTY) *
                          ((nz + zchunk - 1) / zchunk);
   if (used > cv.tiles) return cudaErrorInvalidValue;  // partial buffer too small
   switch (cv.st.R) {
-    case 1: launch_r<T, TL, 1>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
-    case 2: launch_r<T, TL, 2>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
-    case 3: launch_r<T, TL, 3>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
-    case 4: launch_r<T, TL, 4>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
-    case 5: launch_r<T, TL, 5>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
-    case 6: launch_r<T, TL, 6>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
-    case 7: launch_r<T, TL, 7>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
-    default: launch_r<T, TL, 8>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, s); break;
+    case 1: launch_r<T, TL, 1>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, ax, s); break;
+    case 2: launch_r<T, TL, 2>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, ax, s); break;
+    case 3: launch_r<T, TL, 3>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, ax, s); break;
+    case 4: launch_r<T, TL, 4>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, ax, s); break;
+    case 5: launch_r<T, TL, 5>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, ax, s); break;
+    case 6: launch_r<T, TL, 6>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, ax, s); break;
+    case 7: launch_r<T, TL, 7>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, ax, s); break;
+    default: launch_r<T, TL, 8>(cv, x, r, pdir, mask, r_lo, p_lo, x_lo, use_df, p_keep, ax, s); break;
   }
   note_launch();
   return cudaGetLastError();
@@ -347,14 +371,14 @@ cudaError_t cocg_resid(const CocgView<T>& cv, const cpx<T>* x, cpx<T>* r, cpx<T>
 template cudaError_t cocg_resid<double, double>(const CocgView<double>&, const cpx<double>*,
                                                 cpx<double>*, cpx<double>*, int, cpx<double>*,
                                                 cpx<double>*, cpx<double>*, cudaStream_t, bool,
-                                                const cpx<double>*);
+                                                const cpx<double>*, const DfAux*);
 template cudaError_t cocg_resid<double, float>(const CocgView<double>&, const cpx<double>*,
                                                cpx<double>*, cpx<double>*, int, cpx<float>*,
                                                cpx<float>*, cpx<float>*, cudaStream_t, bool,
-                                               const cpx<float>*);
+                                               const cpx<float>*, const DfAux*);
 template cudaError_t cocg_resid<float, float>(const CocgView<float>&, const cpx<float>*,
                                               cpx<float>*, cpx<float>*, int, cpx<float>*,
                                               cpx<float>*, cpx<float>*, cudaStream_t, bool,
-                                               const cpx<float>*);
+                                               const cpx<float>*, const DfAux*);
 
 }  // namespace rpa

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "rpa_internal.cuh"
+
 #include <type_traits>
 
 #ifndef RPA_DOT_F64
@@ -45,6 +47,54 @@ static __device__ __forceinline__ void block_sum_t(T (&v)[NQ], T* sh) {
 #pragma unroll
       for (int q = 0; q < NQ; ++q) v[q] += sh[w * NQ + q];
 }
+
+// ---- double-float arithmetic (each value an unevaluated sum hi + lo of two floats) ------
+struct df {
+  float hi, lo;
+};
+static __device__ __forceinline__ df df_of(double x) {
+  const float h = __double2float_rn(x);
+  return df{h, __double2float_rn(x - (double)h)};
+}
+static __device__ __forceinline__ double df_val(df a) { return (double)a.hi + (double)a.lo; }
+// The error-free transformations below use the _rn intrinsics: they are never contracted
+// into a fused multiply-add, which would round the product and void the exact error terms.
+// s + e = a + b exactly (Knuth's two-sum)
+static __device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// s + e = a + b exactly, |a| >= |b|
+static __device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+static __device__ __forceinline__ df df_add(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+static __device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+// acc + c * x with the product formed exactly in hi (Dekker's product through FMA)
+static __device__ __forceinline__ df df_fma(df acc, df c, df x) {
+  const float p = __fmul_rn(c.hi, x.hi);
+  float e = __fmaf_rn(c.hi, x.hi, -p);
+  e = __fmaf_rn(c.hi, x.lo, __fmaf_rn(c.lo, x.hi, e));
+  const df s = two_sum(acc.hi, p);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, e)));
+}
+static __device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return fast_two_sum(p, e);
+}
+struct cdf {
+  df re, im;
+};
+static __device__ __forceinline__ cdf cdf_of(const cpx<double>& v) { return cdf{df_of(v.re), df_of(v.im)}; }
+// a complex value stored as (re.hi, re.lo, im.hi, im.lo)
+static __device__ __forceinline__ cdf cdf_ld(const float4& v) { return cdf{df{v.x, v.y}, df{v.z, v.w}}; }
 
 // four projector values of one entry (16-byte / 32-byte aligned vector loads)
 static __device__ __forceinline__ void load_chi4(const float* p, float (&c)[4]) {
