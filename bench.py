@@ -469,7 +469,8 @@ def run_ours(args, wl):
                     stride=list(wl["stride"]), interp=wl["interp"],
                     stern_tol=wl["tol"], refine=args.refine, inner_tol=args.inner_tol or "auto",
                     probe_points_per_step=per * wl["nw"] * world, l2="inputs > L2 (no flush)",
-                    tile_rows=tile_rows, tile_rows_tail=tile_tail, cuda_graphs=bool(args.graphs),
+                    tile_rows=tile_rows, tile_rows_tail=tile_tail, cuda_graphs={0: "off", 1: "chunks of 4 iterations, host-checked",
+                                 2: "whole COCG loops (conditional while nodes)"}[args.graphs],
                     h_apply_tiling=(f"{tiling(tile_rows)} (launches over > 32 systems), "
                                     f"{tiling(tile_tail)} (<= 32 systems)"
                                     + (" autotuned" if args.tile == -1 else " set by --tile")),
@@ -620,8 +621,10 @@ def main():
                          "one frequency (options.lanczos_block; mixed form); 1 = scalar")
     ap.add_argument("--lanes", type=int, default=1,
                     help="probe-point lanes run concurrently (options.lanes)")
-    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
-                    help="replay COCG chunks as captured CUDA graphs (1) or launch directly (0)")
+    ap.add_argument("--graphs", type=int, default=2, choices=[0, 1, 2],
+                    help="each COCG loop as one captured graph with device-side loop control "
+                         "(2), COCG chunks as captured graphs replayed by the host (1), or "
+                         "direct launches (0)")
     ap.add_argument("--sweep-interp", action="store_true",
                     help="interpolation study instead of the benchmark line (strides 2, 3 x "
                          "trilinear, tricubic x TF32x3, BF16 projection), one JSON line each")

@@ -106,8 +106,14 @@ typedef struct {
                             two points per thread and a multi-stage asynchronous copy pipeline
                             (mixed form, even nx <= 64, h divides ny); RPA_EINVAL if it does not
                             fit */
-  int graphs;            /* 1: replay each chunk of fused COCG iterations as a captured CUDA
-                            graph (default); 0: launch the kernels one by one */
+  int graphs;            /* 2 (default): each COCG loop runs as one captured CUDA graph whose
+                            conditional while nodes repeat chunks of fused iterations until
+                            no system is active, the active list and counts rebuilt on the
+                            device after every chunk (no host check inside the loop); with
+                            profile = 1 one loop in four runs as with 1.  1: each chunk of
+                            fused iterations is a captured graph replayed by the host, which
+                            reads the active count after every chunk.  0: the kernels are
+                            launched one by one */
   int lanczos_block;     /* 1: scalar Lanczos quadrature per probe (Section 3.1, default);
                             b in 2..8: block Lanczos quadrature, up to b consecutive probe-points
                             of one frequency and distinct grid points share one block

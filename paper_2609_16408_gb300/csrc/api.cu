@@ -112,6 +112,10 @@ struct rpa_ctx {
     int launches = 0;
   };
   std::vector<ChunkGraph> graphs;
+  // COCG loops captured whole (options.graphs = 2): iteration and launch counters of the
+  // running loop, and the loops run so far (profiling samples every kProfLoopEvery-th)
+  DevBuf loopctl_d;
+  long long loop_no = 0;
   int prof_cpx_bytes = 0;
   // non-fatal outcome of the current call (results are still written): RPA_ENOCONV or
   // RPA_EBREAKDOWN (the more severe is kept), with its reason
@@ -509,6 +513,9 @@ constexpr double kDfResidualTol = 1e-8;
 static_assert(kChunkIters <= kChunkItersMax, "counts buffer holds one slot per iteration");
 // with graphs and options.profile, one chunk in kProfEvery is launched directly with events
 constexpr int kProfEvery = 4;
+// with options.graphs = 2 and options.profile, one COCG loop in kProfLoopEvery is run
+// host-checked (with its sample chunks) instead of as one graph
+constexpr int kProfLoopEvery = 4;
 
 template <typename T>
 static FusedBufs<T> make_fused(rpa_ctx* c) {
@@ -692,6 +699,165 @@ static rpa_status run_chunk_graph(rpa_ctx* c, const CocgView<T>& cv, const Fused
   return RPA_OK;
 }
 
+// The whole COCG loop as one CUDA graph, with no host check between chunks (options.graphs
+// = 2).  Launch widths are the power-of-two buckets of the host-checked loop: a prologue
+// chunk (the first iteration starts the recurrence) over W_0 systems, then one level per
+// width W_0 > W_1 > ... > 1, each a while node that repeats its chunk over W_i systems as
+// long as more than W_{i+1} are active.  After every chunk the active list and counts are
+// rebuilt on the device and a one-thread kernel sets the level's condition.  An iteration
+// counter bounds every level (the per-system cap marks every system by maxit + 2 chunks),
+// so each loop ends even if no status changes.  Graphs are cached like the chunk graphs.
+template <typename T>
+static rpa_status run_loop_graph(rpa_ctx* c, const CocgView<T>& cv, const FusedBufs<T>& fb,
+                                 int maxit, int ty_bulk, int ty_tail) {
+  const int nsys = cv.nsys;
+  int w0 = 1;
+  while (w0 < fb.nact) w0 <<= 1;
+  w0 = std::min(w0, nsys);
+  std::vector<int> widths{w0};
+  {
+    int w = 1;
+    while (w < w0) w <<= 1;
+    for (w >>= 1; w >= 1; w >>= 1) widths.push_back(w);
+  }
+  struct Key {
+    int kind, tsize, maxit, w0, ty_bulk, ty_tail;
+    double tol;
+    CocgView<T> cv;
+    FusedBufs<T> fb;
+  } k;
+  std::memset(&k, 0, sizeof(k));  // padding bytes take part in the comparison
+  k.kind = 2;
+  k.tsize = (int)sizeof(T);
+  k.maxit = maxit;
+  k.w0 = w0;
+  k.ty_bulk = ty_bulk;
+  k.ty_tail = ty_tail;
+  k.tol = c->opt.stern_tol;
+  k.cv = cv;
+  k.fb = fb;
+  k.fb.nact = 0;
+  const unsigned char* kb = reinterpret_cast<const unsigned char*>(&k);
+  rpa_ctx::ChunkGraph* hit = nullptr;
+  for (auto& g : c->graphs)
+    if (g.key.size() == sizeof(k) && std::memcmp(g.key.data(), kb, sizeof(k)) == 0) {
+      hit = &g;
+      break;
+    }
+  CK(c->loopctl_d.ensure(2 * sizeof(unsigned long long)));
+  unsigned long long* ctl = c->loopctl_d.as<unsigned long long>();
+  int* cnts = c->counts_d.as<int>();
+  if (!hit) {
+    for (int ty : {ty_bulk, ty_tail}) {  // kernel attributes before capture
+      if (ty > 0) CK(launch_dirmatvec_rows_prepare<T>());
+      if (is_band(ty)) CK(launch_dirmatvec_band_prepare());
+      if (is_x2(ty) && ty != kTileX2) CK(launch_dirmatvec_x2_prepare());
+    }
+    if (c->graphs.size() >= 64) {  // bounded cache: drop the oldest
+      if (c->graphs.front().exec) cudaGraphExecDestroy(c->graphs.front().exec);
+      c->graphs.erase(c->graphs.begin());
+    }
+    const long long l0 = rpa_kernel_launches(c);
+    const int limit = maxit + 2 * kChunkIters;
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+    // chunk of kChunkIters iterations over `width` systems (an even count: p_in / p_out end
+    // as they started), then the active list and counts
+    auto chunk = [&](cudaStream_t s, int width, int first) -> cudaError_t {
+      FusedBufs<T> g = fb;
+      g.nact = width;
+      set_tiling(c, g, width <= kTailSystems ? ty_tail : ty_bulk, width);
+      g.first = first;
+      for (int j = 0; j < kChunkIters; ++j) {
+        const cudaError_t e = fused_iteration<T>(cv, g, c->opt.stern_tol, maxit, s, nullptr);
+        if (e != cudaSuccess) return e;
+        std::swap(g.p_in, g.p_out);
+        g.first = 0;
+      }
+      return count_status(nsys, cv.sysi, cnts, s, c->list_d.as<int>());
+    };
+    // capture fn's launches into graph g after node dep (none if null); *last = its last node
+    auto segment = [&](cudaGraph_t g, cudaGraphNode_t dep, auto&& fn,
+                       cudaGraphNode_t* last) -> cudaError_t {
+      cudaError_t e = cudaStreamBeginCaptureToGraph(c->stream, g, dep ? &dep : nullptr, nullptr,
+                                                    dep ? 1 : 0, mode);
+      if (e != cudaSuccess) return e;
+      const cudaError_t ef = fn(c->stream);
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      const cudaError_t ei =
+          cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+      if (last) *last = (ei == cudaSuccess && nd == 1) ? deps[0] : nullptr;
+      cudaGraph_t out = g;
+      const cudaError_t ee = cudaStreamEndCapture(c->stream, &out);
+      if (ef != cudaSuccess) return ef;
+      if (ei != cudaSuccess) return ei;
+      if (ee != cudaSuccess) return ee;
+      return (last && nd != 1) ? cudaErrorStreamCaptureUnjoined : cudaSuccess;
+    };
+    cudaGraph_t parent = nullptr;
+    cudaError_t err = cudaGraphCreate(&parent, 0);
+    cudaGraphNode_t tail = nullptr;
+    int parent_launches = 0;
+    if (err == cudaSuccess)
+      err = segment(parent, nullptr, [&](cudaStream_t s) -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned long long), s);
+        if (e == cudaSuccess) e = chunk(s, w0, fb.first);
+        return e;
+      }, &tail);
+    parent_launches = (int)(rpa_kernel_launches(c) - l0);
+    for (size_t i = 0; i < widths.size() && err == cudaSuccess; ++i) {
+      const int wnext = i + 1 < widths.size() ? widths[i + 1] : 0;
+      // the prologue's iterations are counted by the first level's check
+      const int add = i == 0 ? kChunkIters : 0;
+      cudaGraphConditionalHandle h;
+      // default 0 at every launch: a level whose check did not run is skipped, never spun
+      err = cudaGraphConditionalHandleCreate(&h, parent, 0, cudaGraphCondAssignDefault);
+      if (err != cudaSuccess) break;
+      const long long lp = rpa_kernel_launches(c);
+      err = segment(parent, tail, [&](cudaStream_t s) {
+        return loop_cond(cnts, ctl, h, wnext, limit, add, 0, s);
+      }, &tail);
+      parent_launches += (int)(rpa_kernel_launches(c) - lp);
+      if (err != cudaSuccess) break;
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t wn = nullptr;
+      err = cudaGraphAddNode(&wn, parent, &tail, nullptr, 1, &np);
+      if (err != cudaSuccess) break;
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      const int width = widths[i];
+      err = segment(body, nullptr, [&](cudaStream_t s) -> cudaError_t {
+        const long long lb = rpa_kernel_launches(c);
+        cudaError_t e = chunk(s, width, 0);
+        if (e != cudaSuccess) return e;
+        const int nb = (int)(rpa_kernel_launches(c) - lb) + 1;  // and the check itself
+        return loop_cond(cnts, ctl, h, wnext, limit, kChunkIters, nb, s);
+      }, nullptr);
+      tail = wn;
+    }
+    note_launch(-(int)(rpa_kernel_launches(c) - l0));  // captured, not launched
+    cudaGraphExec_t exec = nullptr;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, parent, 0);
+    if (parent) cudaGraphDestroy(parent);
+    CK(err);
+    c->graphs.emplace_back();
+    c->graphs.back().key.assign(kb, kb + sizeof(k));
+    c->graphs.back().exec = exec;
+    c->graphs.back().launches = parent_launches;
+    hit = &c->graphs.back();
+  }
+  CK(cudaGraphLaunch(hit->exec, c->stream));
+  unsigned long long hctl[2] = {0, 0};
+  CK(cudaMemcpyAsync(hctl, ctl, sizeof(hctl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  note_launch(hit->launches + (int)hctl[1]);
+  return RPA_OK;
+}
+
 // COCG iterations until no system is active.  Expects r (and x) set for the active systems;
 // forms the projector coefficients of r, then iterates the fused kernels.  With cont, the
 // recurrence continues from the direction kept in p (and its projector coefficients in cp)
@@ -718,6 +884,10 @@ static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv_all, int maxit, bo
     c->prof_stats->tile_rows_tail = ty_tail;
   }
   const bool graphs = c->opt.graphs != 0;
+  // graphs = 2: the whole loop on the device; with profiling, every kProfLoopEvery-th loop
+  // runs host-checked instead, its sample chunks timed with events
+  if (c->opt.graphs == 2 && fb.nact > 0 && !(prof && c->loop_no++ % kProfLoopEvery == 0))
+    return run_loop_graph<T>(c, cv, fb, maxit, ty_bulk, ty_tail);
   const size_t cpxb = sizeof(cpx<T>);
   int chunk_no = 0;
   while (fb.nact > 0) {
@@ -1475,7 +1645,7 @@ rpa_status rpa_default_options(rpa_options* o) {
   o->refine = 4;
   o->inner_tol = 0.0;
   o->tile = -1;
-  o->graphs = 1;
+  o->graphs = 2;
   o->lanczos_block = 1;
   o->refine_restart = 0;
   o->debug_expire_waits = 0;
@@ -1801,7 +1971,7 @@ rpa_status rpa_set_options(rpa_ctx* c, const rpa_options* o) {
   } else if (o->tile < -2) {  // -5 .. -100
     return fail(c, RPA_EINVAL, "bad tile option");
   }
-  if (o->graphs != 0 && o->graphs != 1) return fail(c, RPA_EINVAL, "bad graphs option");
+  if (o->graphs < 0 || o->graphs > 2) return fail(c, RPA_EINVAL, "bad graphs option");
   if (o->lanes < 1 || o->lanes > 8) return fail(c, RPA_EINVAL, "lanes out of range");
   if (o->refine_restart != 0 && o->refine_restart != 1)
     return fail(c, RPA_EINVAL, "bad refine_restart option");

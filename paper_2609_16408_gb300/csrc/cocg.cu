@@ -331,6 +331,15 @@ __global__ void k_count_status(int nsys, const int* __restrict__ sysi, int* __re
     for (int i = sc[kActive] + threadIdx.x; i < nsys; i += blockDim.x) list[i] = -1;
 }
 
+__global__ void k_loop_cond(const int* __restrict__ counts, unsigned long long* __restrict__ ctl,
+                            cudaGraphConditionalHandle h, int wnext, int limit, int add_iters,
+                            int add_launches) {
+  const unsigned long long it = ctl[0] + (unsigned long long)add_iters;
+  ctl[0] = it;
+  ctl[1] += (unsigned long long)add_launches;
+  cudaGraphSetConditional(h, (counts[kActive] > wnext && it <= (unsigned long long)limit) ? 1u : 0u);
+}
+
 // set status for systems: active probes (lanczos flag) -> `on`, others -> kIdle
 __global__ void k_set_status(int nsys, int ns, const int* __restrict__ probe_active, int on,
                              int* __restrict__ sysi) {
@@ -514,6 +523,13 @@ cudaError_t cocg_scalars(int nsys, int tiles, const double* part, double* sysd, 
 
 cudaError_t count_status(int nsys, const int* sysi, int* counts, cudaStream_t s, int* list) {
   k_count_status<<<1, 1024, 0, s>>>(nsys, sysi, counts, list);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t loop_cond(const int* counts, unsigned long long* ctl, cudaGraphConditionalHandle h,
+                      int wnext, int limit, int add_iters, int add_launches, cudaStream_t s) {
+  k_loop_cond<<<1, 1, 0, s>>>(counts, ctl, h, wnext, limit, add_iters, add_launches);
   note_launch();
   return cudaGetLastError();
 }

@@ -101,6 +101,12 @@ cudaError_t count_status(int nsys, const int* sysi, int* counts, cudaStream_t s,
                          int* list = nullptr);
 cudaError_t set_status(int nsys, int ns, const int* probe_active, int on, int* sysi,
                        cudaStream_t s);
+// Loop control of a COCG loop captured as one graph (one thread).  ctl[0] counts the
+// iterations run, ctl[1] the kernels launched: each adds its argument (0 for a pure check).
+// Sets the while-node condition h to 1 while more than wnext systems are active
+// (counts[kActive], as written by count_status) and ctl[0] <= limit, else 0.
+cudaError_t loop_cond(const int* counts, unsigned long long* ctl, cudaGraphConditionalHandle h,
+                      int wnext, int limit, int add_iters, int add_launches, cudaStream_t s);
 cudaError_t remap_status(int nsys, int from, int to, int* sysi, cudaStream_t s);
 template <typename TH, typename TL>
 cudaError_t accumulate(long long nd, int nsys, const int* sysi, int mask, int round,

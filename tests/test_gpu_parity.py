@@ -160,23 +160,32 @@ def test_tile_option_checked():
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_graph_replay_matches_direct_launches(prec):
     """COCG chunks replayed from captured CUDA graphs (grids sized to power-of-two buckets of
-    the active count) agree with kernels launched one by one, and the profiling events
-    captured in the graphs still time the kernels.  The projector sums use atomics, so the
-    two runs agree to the solve tolerance rather than bit for bit."""
+    the active count; graphs = 1) and whole COCG loops captured as one graph with
+    conditional while nodes (graphs = 2, with and without profiling) agree with kernels
+    launched one by one, and the profiling events still time the kernels.  The projector
+    sums use atomics, so the runs agree to the solve tolerance rather than bit for bit."""
     s = sysfix("per")
     out = {}
-    for graphs in (0, 1):
+    for graphs, prof in ((0, 1), (1, 1), (2, 1), (2, 0)):
         c, om, w = ctx_for(s, precision=prec, lanczos_max=3, stern_tol=1e-10, stride=(2, 2, 2),
-                           interp="cubic", stern_maxit=5000, graphs=graphs, profile=1)
+                           interp="cubic", stern_maxit=5000, graphs=graphs, profile=prof)
         P = R.rpa_num_probes(c.ctx)
+        l0 = R.rpa_kernel_launches()
         dco, _, ec, st = R.rpa_energy_density(c.ctx, len(om), P, s.N_d, want_fine=False)
-        out[graphs] = (dco, ec, st)
+        out[graphs, prof] = (dco, ec, st, R.rpa_kernel_launches() - l0)
     rt = 1e-8 if prec == "fp64" else 1e-5
-    assert np.allclose(out[0][0], out[1][0], rtol=rt, atol=rt * np.abs(out[0][0]).max())
-    assert abs(out[0][1] - out[1][1]) <= rt * abs(out[0][1])
-    st = out[1][2]
-    assert abs(st["cocg_iters"] - out[0][2]["cocg_iters"]) <= 0.02 * out[0][2]["cocg_iters"]
-    assert st["kernel_seconds"][1] > 0 and st["kernel_launches"][1] > 0
+    ref = out[0, 1]
+    for key in ((1, 1), (2, 1), (2, 0)):
+        assert np.allclose(ref[0], out[key][0], rtol=rt, atol=rt * np.abs(ref[0]).max()), key
+        assert abs(ref[1] - out[key][1]) <= rt * abs(ref[1]), key
+        st = out[key][2]
+        assert abs(st["cocg_iters"] - ref[2]["cocg_iters"]) <= 0.02 * ref[2]["cocg_iters"], key
+        # the loops launched on the device are counted like the host-launched ones (the
+        # device loop replays whole chunks, so it may run a few more iterations' launches)
+        assert 0.5 * ref[3] <= out[key][3] <= 2.0 * ref[3], (key, out[key][3], ref[3])
+    for key in ((0, 1), (1, 1), (2, 1)):
+        st = out[key][2]
+        assert st["kernel_seconds"][1] > 0 and st["kernel_launches"][1] > 0, key
 
 
 @pytest.mark.parametrize("name", ["per", "dir"])
