@@ -495,6 +495,62 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+def run_uneven(args):
+    """The uneven batch: Si-like cells of 8, 16 and 32 atoms (26^3, 26x26x52, 26x52x52) and
+    the 12-atom Dirichlet cluster (40^3), mixed form, Lanczos early exit at 1e-6 relative
+    change (up to 40 steps), Sternheimer tol 1e-4, each system's full E_c over a coarse set
+    of three points per axis at four frequencies.  Times rpa_batch_energy (every system on its
+    own stream and host thread, kernels of the different grids sharing the GPU) against the
+    same contexts run one after the other, and prints one JSON line."""
+    import time
+
+    import torch
+
+    import paper_2609_16408_gb300 as R
+    import synth
+
+    names = ["si8", "si16", "si32", "cluster12"]
+    om, w = R.rpa_gl_frequencies(4)
+    ctxs, pts = [], []
+    for name in names:
+        s = synth.named_system(name)
+        stride = tuple(max(1, -(-n // 3)) for n in s.n)
+        c = R.Context.from_system(s, om, w, precision="mixed", lanczos_max=40,
+                                  lanczos_rtol=1e-6, stern_tol=1e-4, stern_maxit=20000,
+                                  stride=stride, interp="cubic", refine=args.refine,
+                                  graphs=args.graphs)
+        P = R.rpa_num_probes(c.ctx)
+        ctxs.append((name, s, c, P))
+        pts.append(P * len(om))
+    # warm-up: autotuning, graph capture, workspaces
+    for _ in range(max(1, args.warmup)):
+        R.rpa_batch_energy([c.ctx for _, _, c, _ in ctxs])
+    torch.cuda.synchronize()
+    seq, per = 0.0, {}
+    for name, s, c, P in ctxs:
+        t = time.perf_counter()
+        _, _, ec, st = R.rpa_energy_density(c.ctx, len(om), P, s.N_d, want_fine=False)
+        dt = time.perf_counter() - t
+        seq += dt
+        per[name] = dict(grid=list(s.n), probe_points=P * len(om), seconds=dt, ec=ec,
+                         mean_cocg_iters=st["cocg_iters"] / max(1, st["solves"]),
+                         lanczos_steps_max=st["lanczos_steps_max"])
+    t = time.perf_counter()
+    ec_b, _ = R.rpa_batch_energy([c.ctx for _, _, c, _ in ctxs])
+    bat = time.perf_counter() - t
+    total = float(sum(pts))
+    print(json.dumps(dict(
+        metric="uneven batch: probe-points/s over four grids in one call", unit="probe-pts/s",
+        value=total / bat, sequential_value=total / seq, batch_seconds=bat,
+        sequential_seconds=seq, speedup=seq / bat,
+        ec_batch_equals_sequential=bool(np.allclose(ec_b, [per[n]["ec"] for n in names],
+                                                    rtol=1e-9, atol=0)),
+        systems=per, data="synthetic (seeded cells, synth/)",
+        config=dict(workload="uneven batch (si8, si16, si32, cluster12)", form="mixed",
+                    frequencies=len(om), lanczos_max=40, lanczos_rtol=1e-6, stern_tol=1e-4,
+                    coarse="three points per axis"))), flush=True)
+
+
 def run_interp_sweep(args, wl):
     """Interpolation study (Section 3.2 operators, Section 5.2 metrics) on the workload's cell:
     strides g = 2, 3 x {trilinear, tricubic} x {TF32x3, BF16} projection, against densities
@@ -628,6 +684,9 @@ def main():
     ap.add_argument("--sweep-interp", action="store_true",
                     help="interpolation study instead of the benchmark line (strides 2, 3 x "
                          "trilinear, tricubic x TF32x3, BF16 projection), one JSON line each")
+    ap.add_argument("--uneven", action="store_true",
+                    help="time the uneven batch (four grids in one rpa_batch_energy call) "
+                         "against the same systems run one after the other")
     ap.add_argument("--sweep-nl", type=int, default=3, help="Lanczos steps of the sweep")
     ap.add_argument("--sweep-points", type=int, default=6, help="fine sample points")
     ap.add_argument("--no-fp64", action="store_true")
@@ -651,6 +710,9 @@ def main():
         return
     if args.sweep_interp:
         run_interp_sweep(args, wl)
+        return
+    if args.uneven:
+        run_uneven(args)
         return
     run_ours(args, wl)
 
