@@ -484,7 +484,13 @@ def run_ours(args, wl):
                   solves_per_s=world * tot_solves / t, iters_per_s=world * tot_iters / t,
                   nonconv_solves=sum(st["nonconv_solves"] for st in stats),
                   breakdown_solves=sum(st["breakdown_solves"] for st in stats),
-                  step_statuses=sorted(set(statuses))),
+                  step_statuses=sorted(set(statuses)),
+                  # share of the sampled COCG kernel time in chunks whose launches covered
+                  # at most 32 systems (the latency-bound tail of the slowest solves)
+                  tail_time_fraction=(float(ks[5] / (ks[5] + ks[6]))
+                                      if ks[5] + ks[6] > 0 else None),
+                  tail_iteration_fraction=(float(kl[5] / (kl[5] + kl[6]))
+                                           if kl[5] + kl[6] > 0 else None)),
         oracle_error=oracle_err,
         phases_s=list(np.sum([st["seconds_phase"] for st in stats], axis=0)) if stats else None,
     )
@@ -499,7 +505,7 @@ def run_uneven(args):
     """The uneven batch: Si-like cells of 8, 16 and 32 atoms (26^3, 26x26x52, 26x52x52) and
     the 12-atom Dirichlet cluster (40^3), mixed form, Lanczos early exit at 1e-6 relative
     change (up to 40 steps), Sternheimer tol 1e-4, each system's full E_c over a coarse set
-    of three points per axis at four frequencies.  Times rpa_batch_energy (every system on its
+    of three points per axis (trilinear interpolation) at four frequencies.  Times rpa_batch_energy (every system on its
     own stream and host thread, kernels of the different grids sharing the GPU) against the
     same contexts run one after the other, and prints one JSON line."""
     import time
@@ -517,7 +523,7 @@ def run_uneven(args):
         stride = tuple(max(1, -(-n // 3)) for n in s.n)
         c = R.Context.from_system(s, om, w, precision="mixed", lanczos_max=40,
                                   lanczos_rtol=1e-6, stern_tol=1e-4, stern_maxit=20000,
-                                  stride=stride, interp="cubic", refine=args.refine,
+                                  stride=stride, interp="linear", refine=args.refine,
                                   graphs=args.graphs)
         P = R.rpa_num_probes(c.ctx)
         ctxs.append((name, s, c, P))
@@ -543,12 +549,14 @@ def run_uneven(args):
         metric="uneven batch: probe-points/s over four grids in one call", unit="probe-pts/s",
         value=total / bat, sequential_value=total / seq, batch_seconds=bat,
         sequential_seconds=seq, speedup=seq / bat,
-        ec_batch_equals_sequential=bool(np.allclose(ec_b, [per[n]["ec"] for n in names],
-                                                    rtol=1e-9, atol=0)),
+        # mixed form: atomics in the projector sums make repeated runs differ by rounding
+        ec_batch_vs_sequential_max_rel=float(np.max(np.abs(
+            np.asarray(ec_b) - np.asarray([per[n]["ec"] for n in names])) /
+            np.abs(np.asarray([per[n]["ec"] for n in names])))),
         systems=per, data="synthetic (seeded cells, synth/)",
         config=dict(workload="uneven batch (si8, si16, si32, cluster12)", form="mixed",
                     frequencies=len(om), lanczos_max=40, lanczos_rtol=1e-6, stern_tol=1e-4,
-                    coarse="three points per axis"))), flush=True)
+                    coarse="three points per axis", interp="linear"))), flush=True)
 
 
 def run_interp_sweep(args, wl):

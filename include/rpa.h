@@ -155,7 +155,9 @@ typedef struct {
   /* with options.profile: per COCG kernel class (0 projector dots, 1 H apply (matvec),
    * 2 scalar steps, 3 x/r update, 4 direction update) the summed event time, the number
    * of launches, and the algorithmic bytes moved (active systems x grid points x bytes per
-   * point; projector data and scalars not counted) */
+   * point; projector data and scalars not counted).  Slots 5 and 6 of kernel_seconds: the
+   * time of the sampled chunks whose launches covered at most 32 systems (the tail) and
+   * more (the bulk); slots 5 and 6 of kernel_launches: those chunks' iterations */
   double kernel_seconds[8];
   long long kernel_launches[8];
   double kernel_bytes[8];

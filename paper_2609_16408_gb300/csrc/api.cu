@@ -926,6 +926,7 @@ static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv_all, int maxit, bo
     CKS(counts(c, cv_all.nsys, cnt, true));  // synchronises: the events are complete
     if (sample) {
       rpa_stats* st = c->prof_stats;
+      const int part = width <= kTailSystems ? 5 : 6;  // tail / bulk chunk
       for (int j = 0; j < kChunkIters; ++j) {
         // interval (i, i+1) of iteration j -> kernel class
         static const int cls[6] = {0, 1, 2, 3, 2, 4};
@@ -933,8 +934,10 @@ static rpa_status cocg_loop(rpa_ctx* c, const CocgView<T>& cv_all, int maxit, bo
           float ms = 0.f;
           CK(cudaEventElapsedTime(&ms, c->pev[7 * j + i], c->pev[7 * j + i + 1]));
           st->kernel_seconds[cls[i]] += 1e-3 * ms;
+          st->kernel_seconds[part] += 1e-3 * ms;
           st->kernel_launches[cls[i]] += (i == 1 || i == 3) ? 1 : 0;
         }
+        st->kernel_launches[part] += 1;
         const double pts = (double)c->pinned[kNumStatus * (1 + j) + kActive] * (double)c->nd;
         st->kernel_bytes[1] += pts * 4.0 * cpxb;  // direction + H apply: read r, p; write p, w
         st->kernel_bytes[3] += pts * 6.0 * cpxb;  // update: read x, p, r, w; write x, r
