@@ -368,7 +368,9 @@ def run_ours(args, wl):
                     peak_src=pk["src"] + " (burst copy)",
                     launches=int(kl[dom]), seconds=float(ks[dom]),
                     algorithmic_bytes=float(kb[dom]),
-                    cocg_share=float(ks[dom] / max(1e-30, sum(ks))))
+                    # share of the sampled COCG kernel time (classes 0-4; slots 5 and 6
+                    # split the same time into tail and bulk chunks)
+                    cocg_share=float(ks[dom] / max(1e-30, sum(ks[:5]))))
 
     # FP64 form and mixed form timed on one and the same seeded sample, and the
     # mixed-vs-FP64 error on it

@@ -1335,6 +1335,27 @@ static void drop_lanes(rpa_ctx* c) {
 }
 
 // Run count probe-points in waves; d/alpha/beta/steps are host arrays in input order.
+// Blocks of the block Lanczos quadrature: runs of consecutive entries with one frequency and
+// distinct points, at most bmax long, formed greedily from the first entry (single entries
+// when bmax = 1).  Returns the start of every block and, last, count.
+static std::vector<long long> lanczos_blocks(long long count, const long long* probe,
+                                             const double* omg, int bmax) {
+  std::vector<long long> bstart;
+  for (long long i = 0; i < count;) {
+    long long j = i + 1;
+    while (j < count && j - i < bmax && omg[j] == omg[i]) {
+      bool dup = false;
+      for (long long q = i; q < j; ++q) dup = dup || probe[q] == probe[j];
+      if (dup) break;
+      ++j;
+    }
+    bstart.push_back(i);
+    i = j;
+  }
+  bstart.push_back(count);
+  return bstart;
+}
+
 static rpa_status run_probes(rpa_ctx* c, long long count, const long long* probe,
                              const double* omg, double* d, double* alpha, double* beta,
                              int* steps, rpa_stats* st) {
@@ -1344,21 +1365,8 @@ static rpa_status run_probes(rpa_ctx* c, long long count, const long long* probe
   const int nl = c->opt.lanczos_max;
   const int bmax = c->opt.lanczos_block;
   if (bmax > 1) {
-    // blocks: runs of consecutive entries with one frequency and distinct points, at most
-    // bmax long; waves hold whole blocks
-    std::vector<long long> bstart;
-    for (long long i = 0; i < count;) {
-      long long j = i + 1;
-      while (j < count && j - i < bmax && omg[j] == omg[i]) {
-        bool dup = false;
-        for (long long q = i; q < j; ++q) dup = dup || probe[q] == probe[j];
-        if (dup) break;
-        ++j;
-      }
-      bstart.push_back(i);
-      i = j;
-    }
-    bstart.push_back(count);
+    // waves hold whole blocks
+    const std::vector<long long> bstart = lanczos_blocks(count, probe, omg, bmax);
     const int wave_cap = std::max(nb_max, bmax);
     size_t bi = 0;
     while (bi + 1 < bstart.size()) {
@@ -2111,12 +2119,21 @@ static rpa_status problem_key(rpa_ctx* c, const std::vector<long long>& idx,
   mix(g.h, sizeof(g.h));
   mix(g.bc, sizeof(g.bc));
   mix(&g.fd_radius, sizeof(g.fd_radius));
-  std::vector<double> hv((size_t)c->nd);
-  CK(cudaMemcpy(hv.data(), c->d64.vloc.p, sizeof(double) * c->nd, cudaMemcpyDeviceToHost));
-  mixv(hv);
-  hv.resize((size_t)c->ns * c->nd);
-  CK(cudaMemcpy(hv.data(), c->d64.psi.p, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost));
-  mixv(hv);
+  // device inputs hashed through a bounded host buffer
+  auto mixdev = [&](const void* d, size_t bytes) -> cudaError_t {
+    std::vector<unsigned char> hb(std::min<size_t>(bytes, (size_t)8 << 20));
+    mix(&bytes, sizeof(bytes));
+    for (size_t off = 0; off < bytes; off += hb.size()) {
+      const size_t n = std::min(hb.size(), bytes - off);
+      const cudaError_t e = cudaMemcpy(hb.data(), static_cast<const unsigned char*>(d) + off, n,
+                                       cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return e;
+      mix(hb.data(), n);
+    }
+    return cudaSuccess;
+  };
+  CK(mixdev(c->d64.vloc.p, sizeof(double) * c->nd));
+  CK(mixdev(c->d64.psi.p, sizeof(double) * c->ns * c->nd));
   mixv(c->eps_h);
   mix(&c->hp_ng, sizeof(c->hp_ng));
   mixv(c->hp_nnz);
@@ -2182,15 +2199,30 @@ rpa_status rpa_energy_density(rpa_ctx* c, double* d_coarse, double* d_fine, doub
       if (r.status == RPA_ENOCONV || r.status == RPA_EBREAKDOWN)
         note_soft(c, (rpa_status)r.status, "a solve of an entry resumed from the checkpoint");
     }
-    std::vector<long long> todo;
-    for (long long i = 0; i < count; ++i)
-      if (!done[i]) todo.push_back(i);
+    // Work goes in whole quadrature blocks (block Lanczos: the blocks of the uninterrupted
+    // run, so that a resumed entry shares its block with the same points; a block counts as
+    // done only when all its entries are in the file, else it is recomputed whole).
+    const std::vector<long long> qb =
+        lanczos_blocks(count, pr.data(), om.data(), std::max(1, c->opt.lanczos_block));
+    std::vector<long long> todo, todo_blk;  // undone entries; start of each undone block in todo
+    for (size_t q = 0; q + 1 < qb.size(); ++q) {
+      bool all = true;
+      for (long long i = qb[q]; i < qb[q + 1]; ++i) all = all && done[i];
+      if (all) continue;
+      todo_blk.push_back((long long)todo.size());
+      for (long long i = qb[q]; i < qb[q + 1]; ++i) todo.push_back(i);
+    }
+    todo_blk.push_back((long long)todo.size());
     const long long block =
         (long long)choose_batch(c, (long long)todo.size()) * std::max(1, c->opt.lanes);
     std::vector<long long> bpr;
     std::vector<double> bom, bd;
-    for (size_t b0 = 0; b0 < todo.size(); b0 += (size_t)block) {
-      const size_t n = std::min(todo.size() - b0, (size_t)block);
+    for (size_t q0 = 0; q0 + 1 < todo_blk.size();) {
+      // whole blocks up to `block` entries (at least one block)
+      size_t q1 = q0 + 1;
+      while (q1 + 1 < todo_blk.size() && todo_blk[q1 + 1] - todo_blk[q0] <= block) ++q1;
+      const size_t b0 = (size_t)todo_blk[q0], n = (size_t)(todo_blk[q1] - todo_blk[q0]);
+      q0 = q1;
       bpr.resize(n);
       bom.resize(n);
       bd.assign(n, 0.0);

@@ -126,3 +126,26 @@ def test_checkpoint_keeps_a_nonconverged_status(tmp_path):
         R.rpa_energy_density(c.ctx, nw, P, s.N_d, want_fine=False)
     assert e.value.status == R.RPA_ENOCONV
     assert np.array_equal(_records(path)["d"], rec["d"])
+
+
+def test_checkpoint_keeps_the_blocks_of_block_lanczos(tmp_path):
+    """With block Lanczos quadrature an entry's d depends on the points that share its block,
+    so the file is written in whole blocks of the uninterrupted run, and a block with only
+    some of its entries in the file is recomputed whole: the resumed run gives the
+    uninterrupted run's d (FP64 form, 1e-12 relative)."""
+    s = small()
+    c, om = _ctx(s, lanczos_block=3, batch=4)
+    nw = len(om)
+    P = R.rpa_num_probes(c.ctx)
+    n = P * nw
+    d0, _, ec0, _ = R.rpa_energy_density(c.ctx, nw, P, s.N_d, want_fine=False)
+    path = tmp_path / "blk.ckpt"
+    R.rpa_set_checkpoint(c.ctx, str(path))
+    d1, _, _, _ = R.rpa_energy_density(c.ctx, nw, P, s.N_d, want_fine=False)
+    assert np.allclose(d1, d0, rtol=1e-12, atol=1e-15)
+    # keep 10 records: the block of the 10th-11th entries is then incomplete
+    with open(path, "r+b") as f:
+        f.truncate(HEADER + REC * 10)
+    d2, _, ec2, st2 = R.rpa_energy_density(c.ctx, nw, P, s.N_d, want_fine=False)
+    assert n - 11 <= st2["probe_points"] <= n - 8  # whole blocks recomputed
+    assert np.allclose(d2, d0, rtol=1e-12, atol=1e-15) and abs(ec2 - ec0) <= 1e-12 * abs(ec0)
