@@ -337,6 +337,8 @@ def run_ours(args, wl):
         if t <= -101:
             return (f"bands of {-100 - t} full x rows, two x points per thread, 3-stage "
                     "cp.async pipeline")
+        if t == -6:
+            return "two-point kernel on packed full rows"
         if t in (-3, -4):
             return (f"64 x 8 tiles, two x points per thread, z window in a shared-memory ring, "
                     f"{1 if t == -3 else 2} centre-plane buffer(s)")
@@ -344,6 +346,7 @@ def run_ours(args, wl):
                 else ("64 x 8 tiles, two x points per thread" if t == -2 else "32 x 8 column tiles"))
     hname = ("k_dirmatvec_band" if tile_rows <= -101
              else "k_dirmatvec_rows" if tile_rows > 0
+             else "k_dirmatvec_x2p" if tile_rows == -6
              else ("k_dirmatvec_x2" if tile_rows in (-2, -3, -4) else "k_dirmatvec"))
     names = ["proj_dots", hname, "k_scalars", "k_update_dots", "none"]
     dom = 1 if ks[1] >= ks[3] else 3
@@ -640,7 +643,7 @@ def run_interp_sweep(args, wl):
 
 _KERNEL_FILES = {"k_dirmatvec": "cocg_fused.cu", "k_update_dots": "cocg_fused.cu",
                  "k_dirmatvec_x2": "cocg_x2.cu", "k_dirmatvec_rows": "cocg_rows.cu",
-                 "k_dirmatvec_band": "cocg_band.cu"}
+                 "k_dirmatvec_band": "cocg_band.cu", "k_dirmatvec_x2p": "cocg_x2p.cu"}
 
 
 def kernel_source_sha(kernel="k_dirmatvec"):

@@ -101,7 +101,10 @@ typedef struct {
                             keep the fastest), 0 = 32 x 8 column tiles, -2 = 64 x 8 tiles with
                             two x points per thread (mixed form, even nx), -3 / -4 = the same
                             with each thread's z window in a shared-memory ring instead of
-                            registers (one / two centre-plane buffers), h > 0 = tiles of h
+                            registers (one / two centre-plane buffers), -6 = the two-point
+                            kernel on packed full rows (mixed form, stencil radius 6, even nx
+                            from 26 to 64; not among the autotuned candidates: on the 52^3
+                            grid it measured within 1% of -2), h > 0 = tiles of h
                             full x rows (needs nx <= 64), -100 - h = bands of h full x rows with
                             two points per thread and a multi-stage asynchronous copy pipeline
                             (mixed form, even nx <= 64, h divides ny); RPA_EINVAL if it does not

@@ -545,6 +545,7 @@ static void set_tiling(const rpa_ctx* c, FusedBufs<T>& fb, int ty, int nact) {
   fb.row_ty = ty;
   fb.band_ty = is_band(ty) ? band_rows(ty) : 0;
   fb.ntiles_xy = is_band(ty) ? c->grid.n[1] / band_rows(ty)
+                 : ty == kTileX2Packed ? x2p_tiles_xy(c->grid.n[0], c->grid.n[1])
                  : ty > 0    ? (c->grid.n[1] + ty - 1) / ty
                              : (is_x2(ty) ? x2_tiles_xy(c->grid.n[0], c->grid.n[1])
                                               : fused_ntiles_xy(c));
@@ -579,7 +580,7 @@ static rpa_status choose_tiling(rpa_ctx* c, const CocgView<T>& cv, const FusedBu
     return RPA_OK;
   }
   if (c->tuned_ty[k][0] == -1) {
-    int cand[26];
+    int cand[32];
     int nc = 0;
     cand[nc++] = 0;
     if (sizeof(T) == 4 && x2_tile_fits(c->grid.n[0], c->grid.fd_radius)) {
@@ -594,7 +595,7 @@ static rpa_status choose_tiling(rpa_ctx* c, const CocgView<T>& cv, const FusedBu
       for (int i = 0; i < nb; ++i) cand[nc++] = band_code(bty[i]);
     }
     nc += row_candidates<T>(c->grid.n[0], c->grid.n[1], c->grid.fd_radius, c->ngroup, cand + nc,
-                            16);
+                            std::min(16, 32 - nc));
     int best_ty[2] = {0, 0};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (nc > 1 && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
@@ -1965,7 +1966,11 @@ rpa_status rpa_set_options(rpa_ctx* c, const rpa_options* o) {
     return fail(c, RPA_EINVAL, "bad option");
   for (int a = 0; a < 3; ++a)
     if (o->stride[a] < 1 || o->stride[a] > c->grid.n[a]) return fail(c, RPA_EINVAL, "bad stride");
-  if (is_x2(o->tile)) {
+  if (o->tile == kTileX2Packed) {
+    if (o->precision == RPA_FP64 || !x2p_tile_fits(c->grid.n[0], c->grid.fd_radius))
+      return fail(c, RPA_EINVAL, "packed-row two-point tiles need the mixed form, an even nx "
+                                 "from 26 to 64 and stencil radius 6");
+  } else if (is_x2(o->tile)) {
     if (o->precision == RPA_FP64 || !x2_tile_fits(c->grid.n[0], c->grid.fd_radius))
       return fail(c, RPA_EINVAL, "two-point tiles need the mixed form and an even nx");
   } else if (is_band(o->tile)) {

@@ -369,6 +369,15 @@ cudaError_t launch_dirmatvec_only(const CocgView<T>& cv, const FusedBufs<T>& fb,
       return cudaErrorInvalidValue;  // FP32 only
     }
   }
+  if (fb.row_ty == kTileX2Packed) {
+    if constexpr (sizeof(T) == 4) {
+      cudaError_t e = launch_dirmatvec_x2p(cv, fb, s);
+      note_launch();
+      return e;
+    } else {
+      return cudaErrorInvalidValue;  // FP32 only
+    }
+  }
   if (is_x2(fb.row_ty)) {
     if constexpr (sizeof(T) == 4) {
       cudaError_t e = launch_dirmatvec_x2(cv, fb, s);

@@ -18,7 +18,8 @@ struct FusedBufs {
   int cd_in_smem;          // stage the projector coefficients of a system in shared memory
   int row_ty;              // 0: 32 x 8 column tiles; > 0: row tiles of this height (nx <= 64);
                            // kTileX2: 64 x 8 tiles, two x points per thread (FP32, nx even);
-                           // band_code(h): bands of h full rows, two points per thread
+                           // band_code(h): bands of h full rows, two points per thread;
+                           // kTileX2Packed: two-point kernel on packed full rows
   int band_ty;             // rows of a band (band tiling only)
 };
 
@@ -30,6 +31,12 @@ inline bool is_x2(int code) {
   return code == kTileX2 || code == kTileX2Ring1 || code == kTileX2Ring2;
 }
 cudaError_t launch_dirmatvec_x2_prepare();
+// two-point kernel on packed full rows (see cocg_x2p.cu): FP32, R = 6, even nx in [26, 64]
+constexpr int kTileX2Packed = -6;
+bool x2p_tile_fits(int nx, int R);
+int x2p_tiles_xy(int nx, int ny);
+cudaError_t launch_dirmatvec_x2p(const CocgView<float>& cv, const FusedBufs<float>& fb,
+                                 cudaStream_t s);
 // tiling codes of the band kernel: -100 - h for bands of h rows
 constexpr int kTileBandBase = -100;
 inline int band_code(int ty) { return kTileBandBase - ty; }

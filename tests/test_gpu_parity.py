@@ -33,6 +33,10 @@ SYSTEMS = {
     "dir": lambda: small(bc=(DIRICHLET,) * 3, n=(11, 10, 12), L=(5.5, 5.0, 6.0), seed=7),
     "mix": lambda: small(bc=(PERIODIC, DIRICHLET, PERIODIC), n=(12, 9, 10), L=(6.0, 4.5, 5.0),
                          seed=9, ns=3),
+    # x extents in the range of the packed-row two-point tiles
+    "wide": lambda: small(n=(28, 10, 12), L=(14.0, 5.0, 6.0), seed=11),
+    "wdir": lambda: small(bc=(DIRICHLET, PERIODIC, DIRICHLET), n=(30, 9, 10),
+                          L=(15.0, 4.5, 5.0), seed=13, ns=3),
 }
 _CACHE = {}
 
@@ -110,15 +114,18 @@ def test_chi0_mixed(name):
 @pytest.mark.parametrize("name,tile", [("per", 0), ("per", 1), ("per", 4), ("per", 11),
                                        ("dir", 3), ("dir", 10), ("mix", 2), ("mix", 9),
                                        ("per", -2), ("mix", -2), ("per", -111), ("mix", -109),
-                                       ("per", -3), ("mix", -4)])
+                                       ("per", -3), ("mix", -4), ("wide", -6), ("wdir", -6),
+                                       ("wide", -2)])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_chi0_tilings(name, tile, prec):
-    """Every H-apply tiling (32 x 8 column tiles, 64 x 8 two-point tiles, full-row tiles of
+    """Every H-apply tiling (32 x 8 column tiles, 64 x 8 two-point tiles, two-point tiles on
+    packed full rows (-6: 18 rows of 14 pairs on the 28-point axis, 17 rows of 15 pairs with
+    Dirichlet x and z on the 30-point one), full-row tiles of
     several heights, bands of full rows fed by asynchronous copies (-100 - h), ragged last
     tiles, halos larger than the tile, periodic wrap inside a tile, an x axis shorter than
     twice the padding so that edge pairs wrap to both sides, zero-filled Dirichlet halo rows)
     gives the oracle's chi0 u."""
-    if tile in (-2, -3, -4, -111, -109) and prec == "fp64":
+    if tile in (-2, -3, -4, -6, -111, -109) and prec == "fp64":
         pytest.skip("two-point and band tiles are FP32 kernels")
     s = sysfix(name)
     tol = 1e-12 if prec == "fp64" else 1e-10
@@ -142,6 +149,8 @@ def test_tile_option_checked():
         R.rpa_set_options(c.ctx, precision="fp64", tile=12)  # taller than the grid
     with pytest.raises(RuntimeError):
         R.rpa_set_options(c.ctx, tile=-5)
+    with pytest.raises(RuntimeError):
+        R.rpa_set_options(c.ctx, precision="mixed", tile=-6)  # nx = 10 < 26
     with pytest.raises(RuntimeError):
         R.rpa_set_options(c.ctx, precision="fp64", tile=-2)  # FP32 kernel only
     with pytest.raises(RuntimeError):

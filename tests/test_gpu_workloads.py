@@ -116,15 +116,17 @@ def test_si64_bench_path_vs_oracle():
     c.close()
 
 
-@pytest.mark.parametrize("ty", [13, 26])
-def test_band_tiling_si8_mixed(ty):
-    """Band tiles of the mixed form on the full Si8 grid (26^3, 16 states): two bands of 13
-    rows (halo rows from the neighbouring band and across the periodic wrap) or one band of
-    the whole plane (halo rows wrap onto the band itself); chi0 u against the oracle."""
+@pytest.mark.parametrize("tile", [-113, -126, -6])
+def test_band_tiling_si8_mixed(tile):
+    """Full-row tilings of the mixed form on the full Si8 grid (26^3, 16 states): two bands
+    of 13 rows (halo rows from the neighbouring band and across the periodic wrap), one band
+    of the whole plane (halo rows wrap onto the band itself), and the two-point kernel on
+    packed full rows (19 rows of 13 pairs per tile, a ragged last tile of 7 rows whose halo
+    wraps onto the first tile); chi0 u against the oracle."""
     s = system("si8")
     om, w = oracle.gl_frequencies(2)
     c = R.Context.from_system(s, om, w, precision="mixed", stern_tol=1e-10, refine=4,
-                              stern_maxit=20000, tile=-100 - ty)
+                              stern_maxit=20000, tile=tile)
     rng = np.random.default_rng(31)
     u = rng.standard_normal((1, s.N_d))
     r, _ = R.rpa_chi0(c.ctx, np.array([0.4]), u, s.ns)
