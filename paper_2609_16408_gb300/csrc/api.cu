@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -56,7 +57,7 @@ void DevBuf::release() {
 // ---------------------------------------------------------------------------------------------
 template <typename T>
 struct OpData {
-  DevBuf vloc, psi, g_chi, coef, p_chi, nuV[3], nuVt[3], nuScale;
+  DevBuf vloc, psi, g_chi, coef, p_chi, s_blk, nuV[3], nuVt[3], nuScale;
   Stencil<T> st;
 };
 
@@ -75,7 +76,7 @@ struct rpa_ctx {
   OpData<double> d64;
   OpData<float> d32;
   int ngroup = 0;
-  DevBuf g_off, g_idx, p_off, p_grp;
+  DevBuf g_off, g_idx, p_off, p_grp, s_off, s_nbr;
   DevBuf tile_roff, tile_ranges;  // per 1-D COCG tile: (group, entry range) lists
   DevBuf lam[3];
   // interpolation operators (transposed, coarse x fine) per axis
@@ -226,6 +227,9 @@ static NonlocalDev<T> nlview(rpa_ctx* c) {
   nl.p_off = c->p_off.as<int>();
   nl.p_grp = c->p_grp.as<int>();
   nl.p_chi = o.p_chi.template as<T>();
+  nl.s_off = c->s_off.as<int>();
+  nl.s_nbr = c->s_nbr.as<int>();
+  nl.s_blk = o.s_blk.template as<T>();
   return nl;
 }
 
@@ -532,7 +536,6 @@ static FusedBufs<T> make_fused(rpa_ctx* c) {
   fb.tiles1d = (int)tiles_of(c->nd);
   fb.first = 1;
   fb.nact = 0;
-  fb.cd_in_smem = (sizeof(cpx<T>) * c->ngroup * kProjChunk <= 32768) ? 1 : 0;
   fb.row_ty = 0;
   fb.band_ty = 0;
   return fb;
@@ -1809,6 +1812,53 @@ rpa_status rpa_set_projectors(rpa_ctx* c, int ngroups, const int* nnz, const int
       pgrp[slot] = g;
       for (int l = 0; l < kProjChunk; ++l) pchi[(size_t)slot * kProjChunk + l] = gchi[(size_t)e * kProjChunk + l];
     }
+  // projector overlaps of groups with common support (point-major: every pair of entries at
+  // a point), as 4 x 4 blocks per (group, group) pair, rows by group
+  std::vector<int> soff(NG + 1, 0), snbr;
+  std::vector<double> sblk;
+  {
+    std::vector<std::vector<std::pair<int, std::array<double, 16>>>> rows(NG);
+    for (long long q = 0; q < nd; ++q)
+      for (int e1 = poff[q]; e1 < poff[q + 1]; ++e1)
+        for (int e2 = poff[q]; e2 < poff[q + 1]; ++e2) {
+          auto& row = rows[pgrp[e1]];
+          const int h = pgrp[e2];
+          size_t k = 0;
+          while (k < row.size() && row[k].first != h) ++k;
+          if (k == row.size()) {
+            row.emplace_back(h, std::array<double, 16>{});
+          }
+          for (int l = 0; l < kProjChunk; ++l)
+            for (int m = 0; m < kProjChunk; ++m)
+              row[k].second[l * 4 + m] += pchi[(size_t)e1 * kProjChunk + l] *
+                                          pchi[(size_t)e2 * kProjChunk + m];
+        }
+    for (int g = 0; g < NG; ++g) {
+      std::sort(rows[g].begin(), rows[g].end(),
+                [](const auto& a, const auto& b) { return a.first < b.first; });
+      for (const auto& nb : rows[g]) {
+        snbr.push_back(nb.first);
+        sblk.insert(sblk.end(), nb.second.begin(), nb.second.end());
+      }
+      soff[g + 1] = (int)snbr.size();
+    }
+  }
+  {
+    const size_t nb = std::max<size_t>(snbr.size(), 1);
+    std::vector<float> sblk_f(sblk.begin(), sblk.end());
+    CK(c->s_off.ensure(sizeof(int) * soff.size()));
+    CK(c->s_nbr.ensure(sizeof(int) * nb));
+    CK(c->d64.s_blk.ensure(sizeof(double) * nb * 16));
+    CK(c->d32.s_blk.ensure(sizeof(float) * nb * 16));
+    CK(cudaMemcpy(c->s_off.p, soff.data(), sizeof(int) * soff.size(), cudaMemcpyHostToDevice));
+    if (!snbr.empty()) {
+      CK(cudaMemcpy(c->s_nbr.p, snbr.data(), sizeof(int) * snbr.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(c->d64.s_blk.p, sblk.data(), sizeof(double) * sblk.size(),
+                    cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(c->d32.s_blk.p, sblk_f.data(), sizeof(float) * sblk_f.size(),
+                    cudaMemcpyHostToDevice));
+    }
+  }
   // per 1-D COCG tile (kTile consecutive points): for every group with entries in the tile,
   // the contiguous range of its (index-sorted) group-major entries that falls in the tile
   const long long ntile = (nd + kTile - 1) / kTile;

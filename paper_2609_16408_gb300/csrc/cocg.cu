@@ -211,6 +211,10 @@ __global__ void k_scalars(int nsys, int tiles, int stride, const double* __restr
   double v[4];
   warp_sum_tiles(part + (long long)s * stride * 4, tiles, lane, v);
   if (lane != 0) return;
+  if (kind == 0 || kind == 5) {
+    sd[kNlDot] = 0.0;
+    sd[kNlDot + 1] = 0.0;
+  }
   if (kind == 0) {  // after r0 = b - A x0
     const double rn = sqrt(v[0]), bn = sqrt(v[1]);
     sd[kBnorm] = bn;
@@ -228,6 +232,8 @@ __global__ void k_scalars(int nsys, int tiles, int stride, const double* __restr
       si[kStatus] = kMaxit;
       return;
     }
+    v[0] += sd[kNlDot];
+    v[1] += sd[kNlDot + 1];
     double ar, ai;
     if ((v[0] == 0.0 && v[1] == 0.0) || !isfinite(v[0]) || !isfinite(v[1])) {
       si[kStatus] = kBreakdown;

@@ -12,6 +12,9 @@ constexpr int kTile = 1024;  // grid points per block in the COCG kernels
 constexpr int kSysD = 16;
 constexpr int kRho = 0, kAlpha = 2, kBeta = 4, kBnorm = 6, kTarget = 7, kRnorm = 8,
               kRnormTrue = 9;
+// p^T V_nl p of the current direction (complex), from its projector coefficients (0 without
+// projectors); the H-apply kernels sum p^T (H_loc - sigma) p and the alpha step adds it
+constexpr int kNlDot = 10;
 // per-system ints
 constexpr int kSysI = 4;
 constexpr int kStatus = 0, kIters = 1, kRestarts = 2,

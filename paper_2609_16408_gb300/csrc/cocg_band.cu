@@ -35,7 +35,6 @@ constexpr int kBandMaxThreads = 704;   // 22 warps
 constexpr int kBandSmallThreads = 352;
 constexpr int kBandMaxHalo = 2;        // halo pairs copied per thread and plane
 constexpr size_t kBandSmemMax = 200 * 1024;
-constexpr size_t kBandCdMax = 32 * 1024;  // staged projector coefficients
 
 __device__ __forceinline__ float4 ld4(const cpx<float>* p) {
   return *reinterpret_cast<const float4*>(p);
@@ -67,13 +66,13 @@ __host__ __device__ constexpr int band_pitch() {
   return 64 + 2 * band_xo<R>();
 }
 
-// dynamic shared memory of one block: two centre planes, D stages, staged coefficients
-size_t band_smem(int nx, int R, int ty, int ngroup) {
+// dynamic shared memory of one block: two centre planes and D stages
+size_t band_smem(int nx, int R, int ty) {
   const int xo = R + (R & 1), pitch = 64 + 2 * xo;
   const size_t centre = 2 * sizeof(cpx<float>) * (size_t)(ty + 2 * R) * pitch;
   const size_t stage = (size_t)kBandStages * 2 * sizeof(float4) *
                        ((size_t)ty * (nx / 2) + (size_t)2 * R * (nx / 2));
-  return centre + stage + sizeof(cpx<float>) * (size_t)ngroup * kProjChunk;
+  return centre + stage;
 }
 
 template <int R, bool FIRST, int MAXT>
@@ -95,7 +94,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_dirmatvec_band(CocgView<float> cv, 
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   cpx<T>* cbuf = reinterpret_cast<cpx<T>*>(dyn_smem);
   float4* stg = reinterpret_cast<float4*>(cbuf + 2 * PLN);
-  cpx<T>* scd = reinterpret_cast<cpx<T>*>(stg + D * SSTR);
   __shared__ A sha[32 * 2];
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int y0 = blockIdx.x * TY;
@@ -110,11 +108,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_dirmatvec_band(CocgView<float> cv, 
   const cpx<T> be = mk<T>((T)sd[kBeta], (T)sd[kBeta + 1]);
   const int b = s / cv.ns, n = s - b * cv.ns;
   const cpx<T> sigma = mk<T>((T)cv.eps[n], (T)cv.omega[b]);
-  const int ncd = cv.nl.ngroup * kProjChunk;
-  {
-    const cpx<T>* cd = fb.cp + (long long)s * ncd;
-    for (int i = tid; i < ncd; i += nthr) scd[i] = cd[i];
-  }
   // x padding of every row of both centre planes: zero once (a Dirichlet x axis keeps the
   // zeros; on a periodic axis the owners of the edge pairs overwrite them every plane)
   for (int i = tid; i < 2 * (TY + 2 * R) * 2 * XO; i += nthr) {
@@ -196,35 +189,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_dirmatvec_band(CocgView<float> cv, 
       zb[i] = comb(a.z, a.w, c.z, c.w);
     }
   }
-  const bool has_nl = cv.nl.ngroup > 0;
-  const int* __restrict__ p_off = cv.nl.p_off;
-  const int* __restrict__ p_grp = cv.nl.p_grp;
-  const T* __restrict__ p_chi = cv.nl.p_chi;
-  int ne0 = 0, ne1 = 0, ne2 = 0;
-  if (has_nl && own && z0 < z1) {
-    const int q = own_xy + z0 * plane;
-    ne0 = p_off[q];
-    ne1 = p_off[q + 1];
-    ne2 = p_off[q + 2];
-  }
-  auto proj = [&](cpx<T> a, int e0, int e1) -> cpx<T> {
-    for (int e = e0; e < e1; e += 2) {
-      const bool two = e + 1 < e1;
-      const int g0 = p_grp[e];
-      const int g1 = two ? p_grp[e + 1] : g0;
-      T ch0[kProjChunk], ch1[kProjChunk];
-      load_chi4(p_chi + kProjChunk * e, ch0);
-      if (two) load_chi4(p_chi + kProjChunk * (e + 1), ch1);
-      const cpx<T>* cg0 = scd + kProjChunk * g0;
-      const cpx<T>* cg1 = scd + kProjChunk * g1;
-#pragma unroll
-      for (int l = 0; l < kProjChunk; ++l) {
-        a = caxpy_r(a, ch0[l], cg0[l]);
-        if (two) a = caxpy_r(a, ch1[l], cg1[l]);
-      }
-    }
-    return a;
-  };
   A acc_re = 0, acc_im = 0;
   const T c0 = st.c0;
   for (int z = z0; z < z1; ++z) {
@@ -248,13 +212,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_dirmatvec_band(CocgView<float> cv, 
       const float4 a = sb[2 * j];
       const float4 c = FIRST ? make_float4(0.f, 0.f, 0.f, 0.f) : sb[2 * j + 1];
       st4(cb + hal_slot[k], comb(a.x, a.y, c.x, c.y), comb(a.z, a.w, c.z, c.w));
-    }
-    const int e0 = ne0, e1 = ne1, e2 = ne2;
-    if (has_nl && own && z + 1 < z1) {  // projector ranges of the next plane
-      const int q = own_xy + (z + 1) * plane;
-      ne0 = p_off[q];
-      ne1 = p_off[q + 1];
-      ne2 = p_off[q + 2];
     }
     __syncthreads();
     if (own) {
@@ -289,10 +246,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_dirmatvec_band(CocgView<float> cv, 
         a0 = caxpy_r(a0, st.cz[m], cadd(za[R - m], za[R + m]));
         a1 = caxpy_r(a1, st.cz[m], cadd(zb[R - m], zb[R + m]));
       }
-      if (has_nl) {
-        a0 = proj(a0, e0, e1);
-        a1 = proj(a1, e1, e2);
-      }
       st4(w + q, a0, a1);
       st4(pn + q, c, d);
       acc_re += (A)c.re * a0.re - (A)c.im * a0.im + (A)d.re * a1.re - (A)d.im * a1.im;
@@ -319,7 +272,7 @@ template <int R>
 void launch_r(const CocgView<float>& cv, const FusedBufs<float>& fb, cudaStream_t s) {
   const int ty = fb.band_ty;
   const int thr = ((ty * (cv.st.nx / 2) + 31) / 32) * 32;
-  const size_t smem = band_smem(cv.st.nx, R, ty, cv.nl.ngroup);
+  const size_t smem = band_smem(cv.st.nx, R, ty);
   const dim3 grid(cv.st.ny / ty, fb.nact, fb.nzchunk);
   if (thr <= kBandSmallThreads) {
     if (fb.first)
@@ -372,8 +325,8 @@ bool band_tile_fits(int nx, int ny, int R, int ty, int ngroup) {
   const int thr = ((ty * (nx / 2) + 31) / 32) * 32;
   if (thr < 64 || thr > kBandMaxThreads) return false;
   if (2 * R * (nx / 2) > kBandMaxHalo * thr) return false;  // halo pairs per thread
-  if (sizeof(cpx<float>) * (size_t)ngroup * kProjChunk > kBandCdMax) return false;
-  return band_smem(nx, R, ty, ngroup) <= kBandSmemMax;
+  (void)ngroup;
+  return band_smem(nx, R, ty) <= kBandSmemMax;
 }
 
 int band_candidates(int nx, int ny, int R, int ngroup, int* out, int maxn) {

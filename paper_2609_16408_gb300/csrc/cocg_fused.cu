@@ -17,6 +17,7 @@
 #include "cocg_fused.cuh"
 #include "fused_dev.cuh"
 
+
 namespace rpa {
 
 constexpr int kFTX = 32, kFTY = 8;
@@ -24,9 +25,9 @@ constexpr int kFTX = 32, kFTY = 8;
 // Direction update + H apply, 2.5-D blocked (see the file comment).  All offsets inside a
 // system are 32-bit (N_d < 2^31); stencil neighbours are read from shared memory at
 // compile-time offsets from a per-thread base; FIRST marks the first iteration of a solve
-// (p_k = r_k, no previous direction).  The projector coefficients of the system are in
-// shared memory when SMEM_CD, else read through the read-only path.
-template <typename T, int R, bool FIRST, bool SMEM_CD>
+// (p_k = r_k, no previous direction).  The projector term of w is added by the update
+// kernel (k_update_dots); this kernel applies the local part of H - sigma.
+template <typename T, int R, bool FIRST>
 __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
     k_dirmatvec(CocgView<T> cv, FusedBufs<T> fb) {
   const int s = cv.list ? cv.list[blockIdx.y] : blockIdx.y;
@@ -36,8 +37,6 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
   constexpr int NHALO = PLN - kFTX * kFTY;
   constexpr int HPT = (NHALO + kFTX * kFTY - 1) / (kFTX * kFTY);
   __shared__ cpx<T> pl[2 * PLN];
-  __shared__ T sh[8 * 2];
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
   const Stencil<T>& st = cv.st;
   const int nx = st.nx, ny = st.ny, nz = st.nz;
   const int plane = nx * ny;
@@ -57,13 +56,6 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
   const cpx<T> be = mk<T>((T)sd[kBeta], (T)sd[kBeta + 1]);
   const int b = s / cv.ns, n = s - b * cv.ns;
   const cpx<T> sigma = mk<T>((T)cv.eps[n], (T)cv.omega[b]);
-  const int ncd = cv.nl.ngroup * kProjChunk;
-  const cpx<T>* cd = fb.cp + (long long)s * ncd;
-  if (SMEM_CD) {
-    cpx<T>* scd = reinterpret_cast<cpx<T>*>(dyn_smem);
-    for (int i = threadIdx.x; i < ncd; i += blockDim.x) scd[i] = cd[i];
-    cd = scd;  // read after the first barrier of the z loop
-  }
   // xy offsets (fixed along z) of the own column and of this thread's halo elements
   int own_xy;
   {
@@ -125,24 +117,12 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
     zq[i] = comb(rv, pv);
   }
   cpx<T> nq_r, nq_p, h_r[HPT], h_p[HPT];
-  const bool has_nl = cv.nl.ngroup > 0;
-  const int* __restrict__ p_off = cv.nl.p_off;
-  const int* __restrict__ p_grp = cv.nl.p_grp;
-  const T* __restrict__ p_chi = cv.nl.p_chi;
-  // next plane's potential value, projector range and first two projector entries are
-  // fetched with its stencil inputs so that their latency overlaps the current plane
-  int ne0 = 0, ne1 = 0;
   auto prefetch = [&](int z) {
     const int zo = zoff(z + R);
     ld((zo < 0 || own_xy < 0) ? -1 : zo + own_xy, nq_r, nq_p);
     const int zp = z * plane;
 #pragma unroll
     for (int k = 0; k < HPT; ++k) ld(halo_xy[k] < 0 ? -1 : zp + halo_xy[k], h_r[k], h_p[k]);
-    if (has_nl && valid) {
-      const int q = own_xy + zp;
-      ne0 = p_off[q];
-      ne1 = p_off[q + 1];
-    }
   };
   if (z0 < z1) prefetch(z0);
   using A = dacc_t<T>;
@@ -155,7 +135,6 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
 #pragma unroll
     for (int k = 0; k < HPT; ++k)
       if (halo_s[k]) halo_s[k][bo] = comb(h_r[k], h_p[k]);
-    const int e0 = ne0, e1 = ne1;
     if (z + 1 < z1) prefetch(z + 1);  // in flight while this plane is computed
     __syncthreads();
     if (valid) {
@@ -170,21 +149,6 @@ __global__ void __launch_bounds__(kFTX * kFTY, sizeof(T) == 4 ? 3 : 2)
         a = caxpy_r(a, st.cx[m], cadd(cs[-m], cs[m]));
         a = caxpy_r(a, st.cy[m], cadd(cs[-m * EXN], cs[m * EXN]));
         a = caxpy_r(a, st.cz[m], cadd(zq[R - m], zq[R + m]));
-      }
-      for (int e = e0; e < e1; e += 2) {  // the rest, two entries in flight per step
-        const bool two = e + 1 < e1;
-        const int g0 = p_grp[e];
-        const int g1 = two ? p_grp[e + 1] : g0;
-        T ch0[kProjChunk], ch1[kProjChunk];
-        load_chi4(p_chi + kProjChunk * e, ch0);
-        if (two) load_chi4(p_chi + kProjChunk * (e + 1), ch1);
-        const cpx<T>* cg0 = cd + kProjChunk * g0;
-        const cpx<T>* cg1 = cd + kProjChunk * g1;
-#pragma unroll
-        for (int l = 0; l < kProjChunk; ++l) {
-          a = caxpy_r(a, ch0[l], cg0[l]);
-          if (two) a = caxpy_r(a, ch1[l], cg1[l]);
-        }
       }
       w[q] = a;
       pn[q] = c;
@@ -216,6 +180,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_update_dots(Coc
   if (s < 0 || cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
   __shared__ double sh[8 * 3];
   __shared__ cpx<T> sr[kTile];
+  __shared__ cpx<T> swn[kTile];  // projector term V_nl p of the tile's points
   const long long nd = cv.nd;
   const double* sd = cv.sysd + (long long)s * kSysD;
   const cpx<T> al = mk<T>((T)sd[kAlpha], (T)sd[kAlpha + 1]);
@@ -240,28 +205,43 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_update_dots(Coc
       rv0[u] = rr_[p];
     }
   }
+  // w holds the local part (H_loc - sigma) p only.  Without projectors r_{k+1} = r - alpha w
+  // is final at once.  With them one pass over the tile's projector entries, whole warps per
+  // projector group (entries of a group in the tile are one contiguous range of distinct
+  // points), both adds chi * cp (the projector term V_nl p) to the tile's points in shared
+  // memory and forms the sums chi^T rhat of rhat = r - alpha w_loc, reduced with shuffles
+  // and added to cr[s][g][l] with one atomic per value; r_{k+1} = rhat - alpha V_nl p follows
+  // after the pass, and the part alpha chi^T V_nl p = alpha S cp of the sums is taken off
+  // per system afterwards (k_proj_next).
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const long long p = t0 + threadIdx.x + u * 256;
     if (p < t1) {
       xx_[p] = cadd(xv[u], cmul(al, pv[u]));
       const cpx<T> rv = csub(rv0[u], cmul(al, wv[u]));
-      rr_[p] = rv;
-      if (nl) sr[p - t0] = rv;
-      a0 += (A)rv.re * rv.re + (A)rv.im * rv.im;
-      a1 += (A)rv.re * rv.re - (A)rv.im * rv.im;
-      a2 += (A)2 * rv.re * rv.im;
+      if (nl) {
+        sr[p - t0] = rv;
+        swn[p - t0] = mk<T>((T)0, (T)0);
+      } else {
+        rr_[p] = rv;
+        a0 += (A)rv.re * rv.re + (A)rv.im * rv.im;
+        a1 += (A)rv.re * rv.re - (A)rv.im * rv.im;
+        a2 += (A)2 * rv.re * rv.im;
+      }
     }
   }
-  A acc[3] = {a0, a1, a2};
   if (nl) {
     __syncthreads();
     cpx<T>* cr = fb.cr + (long long)s * cv.nl.ngroup * kProjChunk;
+    const cpx<T>* cpg = fb.cp + (long long)s * cv.nl.ngroup * kProjChunk;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q0 = fb.tile_roff[blockIdx.x], q1 = fb.tile_roff[blockIdx.x + 1];
     for (int q = q0 + warp; q < q1; q += (int)(blockDim.x >> 5)) {
       const int g = fb.tile_ranges[3 * q], e0 = fb.tile_ranges[3 * q + 1],
                 e1 = fb.tile_ranges[3 * q + 2];
+      cpx<T> cg[kProjChunk];
+#pragma unroll
+      for (int l = 0; l < kProjChunk; ++l) cg[l] = cpg[g * kProjChunk + l];
       T a[2 * kProjChunk];
 #pragma unroll
       for (int i = 0; i < 2 * kProjChunk; ++i) a[i] = (T)0;
@@ -279,12 +259,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_update_dots(Coc
           load_chi4(cv.nl.g_chi + (long long)en * kProjChunk, chn);
         }
         const cpx<T> rv = sr[ix - t0];
+        cpx<T> v = mk<T>((T)0, (T)0);
 #pragma unroll
         for (int l = 0; l < kProjChunk; ++l) {
           a[2 * l] += ch[l] * rv.re;
           a[2 * l + 1] += ch[l] * rv.im;
+          v = caxpy_r(v, ch[l], cg[l]);
           ch[l] = chn[l];
         }
+        atomicAdd(&swn[ix - t0].re, v.re);
+        atomicAdd(&swn[ix - t0].im, v.im);
         ix = ixn;
         e = en;
       }
@@ -306,7 +290,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_update_dots(Coc
         atomicAdd(&cr[g * kProjChunk + lane].im, cf * im);
       }
     }
+    __syncthreads();
+    for (long long p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
+      const cpx<T> rv = csub(sr[p - t0], cmul(al, swn[p - t0]));
+      rr_[p] = rv;
+      a0 += (A)rv.re * rv.re + (A)rv.im * rv.im;
+      a1 += (A)rv.re * rv.re - (A)rv.im * rv.im;
+      a2 += (A)2 * rv.re * rv.im;
+    }
   }
+  A acc[3] = {a0, a1, a2};
   block_sum_t<A, 3>(acc, reinterpret_cast<A*>(sh));
   if (threadIdx.x == 0) {
     double* pp = cv.part + ((long long)s * cv.tiles + blockIdx.x) * 4;
@@ -316,46 +309,92 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_update_dots(Coc
   }
 }
 
-// S2 with the projector bookkeeping: after the scalar step (kind 2), every still-active
-// system forms cp = cr + beta cp and clears cr.  One warp per system.
+// S2 with the projector bookkeeping.  After the scalar step (kind 2), every still-active
+// system forms cp = cr + beta cp and clears cr.  One block per system.  With corr, cr holds
+// the sums chi^T rhat of the update kernel (rhat = r - alpha w_loc): the projector part
+// alpha chi^T V_nl p = alpha S cp is taken off first, S the projector overlap blocks, with
+// the system's cp (still that of the last direction) staged in shared memory.  Then
+// p^T V_nl p = sum over projectors of cp^2 / (gamma dV) (cp = gamma dV chi^T p; unconjugated
+// square) goes to sysd[kNlDot] for the next alpha step.
+constexpr int kProjNextThreads = 128;
 template <typename T>
-__global__ void k_proj_next(int nsys, int ngroup, const double* __restrict__ sysd,
-                            const int* __restrict__ sysi, int init, cpx<T>* __restrict__ cp,
-                            cpx<T>* __restrict__ cr, const int* __restrict__ list) {
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kProjNextThreads)
+    k_proj_next(int nsys, NonlocalDev<T> nl, double* __restrict__ sysd,
+                const int* __restrict__ sysi, int init, cpx<T>* __restrict__ cp,
+                cpx<T>* __restrict__ cr, const int* __restrict__ list, int corr, int stage) {
+  const int i = blockIdx.x;
   if (i >= nsys) return;
   const int s = list ? list[i] : i;
   if (s < 0 || sysi[(long long)s * kSysI + kStatus] != kActive) return;
-  const double* sd = sysd + (long long)s * kSysD;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  // ngroup x 4 coefficients of the system (corr; read in place when they exceed 48 KB)
+  cpx<T>* scp = reinterpret_cast<cpx<T>*>(dyn_smem);
+  const int ngroup = nl.ngroup, nv = ngroup * kProjChunk;
+  double* sd = sysd + (long long)s * kSysD;
   const cpx<T> be = init ? mk<T>((T)0, (T)0) : mk<T>((T)sd[kBeta], (T)sd[kBeta + 1]);
-  cpx<T>* p = cp + (long long)s * ngroup * kProjChunk;
-  cpx<T>* q = cr + (long long)s * ngroup * kProjChunk;
-  for (int i = lane; i < ngroup * kProjChunk; i += 32) {
-    p[i] = init ? q[i] : cadd(q[i], cmul(be, p[i]));
-    q[i] = mk<T>((T)0, (T)0);
+  cpx<T>* p = cp + (long long)s * nv;
+  cpx<T>* q = cr + (long long)s * nv;
+  if (corr) {
+    if (stage) {
+      for (int j = threadIdx.x; j < nv; j += blockDim.x) scp[j] = p[j];
+      __syncthreads();
+    } else {
+      scp = p;
+    }
+    const cpx<T> al = mk<T>((T)sd[kAlpha], (T)sd[kAlpha + 1]);
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+      const int g = j / kProjChunk, l = j - g * kProjChunk;
+      cpx<T> v = mk<T>((T)0, (T)0);
+      const int k0 = nl.s_off[g], k1 = nl.s_off[g + 1];
+#pragma unroll 4
+      for (int k = k0; k < k1; ++k) {
+        const T* blk = nl.s_blk + (long long)k * 16 + l * 4;
+        const cpx<T>* ph = scp + nl.s_nbr[k] * kProjChunk;
+#pragma unroll
+        for (int m = 0; m < kProjChunk; ++m) v = caxpy_r(v, blk[m], ph[m]);
+      }
+      q[j] = csub(q[j], cmul(al, mk<T>(nl.coef[j] * v.re, nl.coef[j] * v.im)));
+    }
   }
+  double dre = 0.0, dim = 0.0;
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    const cpx<T> v = init ? q[j] : cadd(q[j], cmul(be, p[j]));
+    p[j] = v;
+    q[j] = mk<T>((T)0, (T)0);
+    const double cf = (double)nl.coef[j];
+    if (cf != 0.0) {
+      const double a = (double)v.re, b = (double)v.im;
+      dre += (a * a - b * b) / cf;
+      dim += 2.0 * a * b / cf;
+    }
+  }
+  double acc[2] = {dre, dim};
+  __shared__ double shd[(kProjNextThreads / 32) * 2];
+  block_sum_t<double, 2>(acc, shd);
+  if (threadIdx.x == 0) {
+    sd[kNlDot] = acc[0];
+    sd[kNlDot + 1] = acc[1];
+  }
+}
+
+template <typename T>
+static void launch_proj_next(const CocgView<T>& cv, const FusedBufs<T>& fb, int nsys,
+                             const int* list, int init, int corr, cudaStream_t s) {
+  size_t smem = corr ? sizeof(cpx<T>) * cv.nl.ngroup * kProjChunk : 0;
+  const int stage = smem > 0 && smem <= 48 * 1024;
+  if (!stage) smem = 0;
+  k_proj_next<T><<<nsys, kProjNextThreads, smem, s>>>(nsys, cv.nl, cv.sysd, cv.sysi, init,
+                                                      fb.cp, fb.cr, list, corr, stage);
 }
 
 // -------------------------------------------------------------------------------------------
 template <typename T, int R>
 static void launch_dirmatvec(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s) {
-  // the coefficients go to shared memory only while static + dynamic stay within 48 KB
-  constexpr size_t kPlanes = 2 * sizeof(cpx<T>) * (kFTX + 2 * R) * (kFTY + 2 * R);
-  size_t cdb = fb.cd_in_smem ? sizeof(cpx<T>) * cv.nl.ngroup * kProjChunk : 0;
-  if (cdb + kPlanes + 1024 > 48 * 1024) cdb = 0;
   dim3 grid(fb.ntiles_xy, fb.nact, fb.nzchunk);
-  if (fb.first) {
-    if (cdb)
-      k_dirmatvec<T, R, true, true><<<grid, kFTX * kFTY, cdb, s>>>(cv, fb);
-    else
-      k_dirmatvec<T, R, true, false><<<grid, kFTX * kFTY, 0, s>>>(cv, fb);
-  } else {
-    if (cdb)
-      k_dirmatvec<T, R, false, true><<<grid, kFTX * kFTY, cdb, s>>>(cv, fb);
-    else
-      k_dirmatvec<T, R, false, false><<<grid, kFTX * kFTY, 0, s>>>(cv, fb);
-  }
+  if (fb.first)
+    k_dirmatvec<T, R, true><<<grid, kFTX * kFTY, 0, s>>>(cv, fb);
+  else
+    k_dirmatvec<T, R, false><<<grid, kFTX * kFTY, 0, s>>>(cv, fb);
 }
 
 template <typename T>
@@ -431,8 +470,7 @@ cudaError_t fused_iteration(const CocgView<T>& cv, const FusedBufs<T>& fb, doubl
                    maxit, 0, s, cv.tiles, cv.list);
   if (e != cudaSuccess) return e;
   if (cv.nl.ngroup > 0) {
-    k_proj_next<T><<<(fb.nact + 3) / 4, 128, 0, s>>>(fb.nact, cv.nl.ngroup, cv.sysd, cv.sysi, 0,
-                                                     fb.cp, fb.cr, cv.list);
+    launch_proj_next<T>(cv, fb, fb.nact, cv.list, 0, 1, s);
     note_launch();
   }
   if (ev) cudaEventRecord(ev[5], s);
@@ -445,8 +483,7 @@ template <typename T>
 cudaError_t fused_prepare(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s,
                           int init) {
   if (cv.nl.ngroup == 0) return cudaSuccess;
-  k_proj_next<T><<<(cv.nsys + 3) / 4, 128, 0, s>>>(cv.nsys, cv.nl.ngroup, cv.sysd, cv.sysi, init,
-                                                   fb.cp, fb.cr, nullptr);
+  launch_proj_next<T>(cv, fb, cv.nsys, nullptr, init, 0, s);
   note_launch();
   return cudaGetLastError();
 }

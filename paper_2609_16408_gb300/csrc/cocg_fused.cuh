@@ -15,7 +15,6 @@ struct FusedBufs {
   const int* tile_ranges;  // (group, first entry, end entry) of group-major entries in a tile
   int ntiles_xy, nzchunk, zchunk, tiles1d, first;
   int nact;                // launched systems: the first nact entries of CocgView::list
-  int cd_in_smem;          // stage the projector coefficients of a system in shared memory
   int row_ty;              // 0: 32 x 8 column tiles; > 0: row tiles of this height (nx <= 64);
                            // kTileX2: 64 x 8 tiles, two x points per thread (FP32, nx even);
                            // band_code(h): bands of h full rows, two points per thread;

@@ -32,7 +32,7 @@ constexpr int row_max_threads() {
 
 template <typename T, int R, bool FIRST>
 __global__ void __launch_bounds__(row_max_threads<T>())
-    k_dirmatvec_rows(CocgView<T> cv, FusedBufs<T> fb, int ty, int smem_cd) {
+    k_dirmatvec_rows(CocgView<T> cv, FusedBufs<T> fb, int ty) {
   const int s = cv.list ? cv.list[blockIdx.y] : blockIdx.y;
   if (s < 0 || cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
   const Stencil<T>& st = cv.st;
@@ -62,13 +62,6 @@ __global__ void __launch_bounds__(row_max_threads<T>())
   const cpx<T> be = mk<T>((T)sd[kBeta], (T)sd[kBeta + 1]);
   const int b = s / cv.ns, n = s - b * cv.ns;
   const cpx<T> sigma = mk<T>((T)cv.eps[n], (T)cv.omega[b]);
-  const int ncd = cv.nl.ngroup * kProjChunk;
-  const cpx<T>* cd = fb.cp + (long long)s * ncd;
-  if (smem_cd) {
-    cpx<T>* scd = pl + 2 * PLN;
-    for (int i = tid; i < ncd; i += blockDim.x) scd[i] = cd[i];
-    cd = scd;
-  }
   // in-plane offsets of this thread's own point and of its halo elements (fixed along z)
   int own_xy = -1;
   if (inblk) {
@@ -134,22 +127,12 @@ __global__ void __launch_bounds__(row_max_threads<T>())
     zq[i] = comb(rv, pv);
   }
   cpx<T> nq_r, nq_p, h_r[kRowMaxHalo], h_p[kRowMaxHalo];
-  const bool has_nl = cv.nl.ngroup > 0;
-  const int* __restrict__ p_off = cv.nl.p_off;
-  const int* __restrict__ p_grp = cv.nl.p_grp;
-  const T* __restrict__ p_chi = cv.nl.p_chi;
-  int ne0 = 0, ne1 = 0;
   auto prefetch = [&](int z) {
     const int zo = zoff(z + R);
     ld((zo < 0 || own_xy < 0) ? -1 : zo + own_xy, nq_r, nq_p);
     const int zp = z * plane;
 #pragma unroll
     for (int k = 0; k < kRowMaxHalo; ++k) ld(halo_xy[k] < 0 ? -1 : zp + halo_xy[k], h_r[k], h_p[k]);
-    if (has_nl && valid) {
-      const int q = own_xy + zp;
-      ne0 = p_off[q];
-      ne1 = p_off[q + 1];
-    }
   };
   if (z0 < z1) prefetch(z0);
   using A = dacc_t<T>;
@@ -169,7 +152,6 @@ __global__ void __launch_bounds__(row_max_threads<T>())
       ld(xy < 0 ? -1 : z * plane + xy, rv, pv);
       pl[bo + slot] = comb(rv, pv);
     }
-    const int e0 = ne0, e1 = ne1;
     if (z + 1 < z1) prefetch(z + 1);
     __syncthreads();
     if (valid) {
@@ -184,21 +166,6 @@ __global__ void __launch_bounds__(row_max_threads<T>())
         a = caxpy_r(a, st.cx[m], cadd(cs[-m], cs[m]));
         a = caxpy_r(a, st.cy[m], cadd(cs[-m * EXN], cs[m * EXN]));
         a = caxpy_r(a, st.cz[m], cadd(zq[R - m], zq[R + m]));
-      }
-      for (int e = e0; e < e1; e += 2) {
-        const bool two = e + 1 < e1;
-        const int g0 = p_grp[e];
-        const int g1 = two ? p_grp[e + 1] : g0;
-        T ch0[kProjChunk], ch1[kProjChunk];
-        load_chi4(p_chi + kProjChunk * e, ch0);
-        if (two) load_chi4(p_chi + kProjChunk * (e + 1), ch1);
-        const cpx<T>* cg0 = cd + kProjChunk * g0;
-        const cpx<T>* cg1 = cd + kProjChunk * g1;
-#pragma unroll
-        for (int l = 0; l < kProjChunk; ++l) {
-          a = caxpy_r(a, ch0[l], cg0[l]);
-          if (two) a = caxpy_r(a, ch1[l], cg1[l]);
-        }
       }
       w[q] = a;
       pn[q] = c;
@@ -225,11 +192,10 @@ void launch_r(const CocgView<T>& cv, const FusedBufs<T>& fb, cudaStream_t s) {
   const dim3 grid(fb.ntiles_xy, fb.nact, fb.nzchunk);
   const int thr = ((cv.st.nx * ty + 31) / 32) * 32;
   const size_t pls = 2 * sizeof(cpx<T>) * (size_t)(cv.st.nx + 2 * R) * (ty + 2 * R);
-  const size_t cdb = fb.cd_in_smem ? sizeof(cpx<T>) * cv.nl.ngroup * kProjChunk : 0;
   if (fb.first)
-    k_dirmatvec_rows<T, R, true><<<grid, thr, pls + cdb, s>>>(cv, fb, ty, fb.cd_in_smem);
+    k_dirmatvec_rows<T, R, true><<<grid, thr, pls, s>>>(cv, fb, ty);
   else
-    k_dirmatvec_rows<T, R, false><<<grid, thr, pls + cdb, s>>>(cv, fb, ty, fb.cd_in_smem);
+    k_dirmatvec_rows<T, R, false><<<grid, thr, pls, s>>>(cv, fb, ty);
 }
 
 constexpr int kRowSmemMax = 160 * 1024;
@@ -266,9 +232,9 @@ bool row_tile_fits(int nx, int ny, int R, int ty) {
   if (nx > 64 || R < 1 || R > 8 || ty < 1 || ty > ny) return false;
   const int thr = ((nx * ty + 31) / 32) * 32;
   if (thr > row_max_threads<T>()) return false;
-  // two planes with halo plus up to 32 KB of staged projector coefficients
+  // two planes with halo
   const size_t pls = 2 * sizeof(cpx<T>) * (size_t)(nx + 2 * R) * (ty + 2 * R);
-  return pls + 32768 <= (size_t)kRowSmemMax;
+  return pls <= (size_t)kRowSmemMax;
 }
 template bool row_tile_fits<float>(int, int, int, int);
 template bool row_tile_fits<double>(int, int, int, int);

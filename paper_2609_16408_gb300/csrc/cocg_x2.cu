@@ -44,9 +44,9 @@ constexpr size_t x2_ring_bytes() {
   return (size_t)(2 * R + 1) * kX2Threads * sizeof(float4);
 }
 
-template <int R, bool FIRST, bool SMEM_CD, int ZM>
+template <int R, bool FIRST, int ZM>
 __global__ void __launch_bounds__(kX2Threads, ZM == kZRing1 ? 3 : 2)
-    k_dirmatvec_x2(CocgView<float> cv, FusedBufs<float> fb, int ring_off) {
+    k_dirmatvec_x2(CocgView<float> cv, FusedBufs<float> fb) {
   using T = float;
   const int s = cv.list ? cv.list[blockIdx.y] : blockIdx.y;
   if (s < 0 || cv.sysi[(long long)s * kSysI + kStatus] != kActive) return;
@@ -59,9 +59,8 @@ __global__ void __launch_bounds__(kX2Threads, ZM == kZRing1 ? 3 : 2)
   constexpr int NHALO = NUSED - kX2TX * kX2TY;
   constexpr int HPT = (NHALO + kX2Threads - 1) / kX2Threads;
   __shared__ __align__(16) cpx<T> pl[(ZM == kZRing1 ? 1 : 2) * PLN];
-  __shared__ T sh[8 * 2];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  float4* ring = reinterpret_cast<float4*>(dyn_smem + ring_off);  // NQ x kX2Threads (RING)
+  float4* ring = reinterpret_cast<float4*>(dyn_smem);  // NQ x kX2Threads (RING)
   const Stencil<T>& st = cv.st;
   const int nx = st.nx, ny = st.ny, nz = st.nz;
   const int plane = nx * ny;
@@ -81,13 +80,6 @@ __global__ void __launch_bounds__(kX2Threads, ZM == kZRing1 ? 3 : 2)
   const cpx<T> be = mk<T>((T)sd[kBeta], (T)sd[kBeta + 1]);
   const int b = s / cv.ns, n = s - b * cv.ns;
   const cpx<T> sigma = mk<T>((T)cv.eps[n], (T)cv.omega[b]);
-  const int ncd = cv.nl.ngroup * kProjChunk;
-  const cpx<T>* cd = fb.cp + (long long)s * ncd;
-  if (SMEM_CD) {
-    cpx<T>* scd = reinterpret_cast<cpx<T>*>(dyn_smem);
-    for (int i = threadIdx.x; i < ncd; i += blockDim.x) scd[i] = cd[i];
-    cd = scd;  // read after the first barrier of the z loop
-  }
   // xy offset of the pair (its first point; -1 outside a Dirichlet boundary)
   int own_xy;
   {
@@ -173,41 +165,12 @@ __global__ void __launch_bounds__(kX2Threads, ZM == kZRing1 ? 3 : 2)
     }
   }
   cpx<T> nr0, nr1, np0, np1, h_r[HPT], h_p[HPT];
-  const bool has_nl = cv.nl.ngroup > 0;
-  const int* __restrict__ p_off = cv.nl.p_off;
-  const int* __restrict__ p_grp = cv.nl.p_grp;
-  const T* __restrict__ p_chi = cv.nl.p_chi;
-  int ne0 = 0, ne1 = 0, ne2 = 0;
   auto prefetch = [&](int z) {
     const int zo = zoff(z + R);
     ld2((zo < 0 || own_xy < 0) ? -1 : zo + own_xy, nr0, nr1, np0, np1);
     const int zp = z * plane;
 #pragma unroll
     for (int k = 0; k < HPT; ++k) ld1(halo_xy[k] < 0 ? -1 : zp + halo_xy[k], h_r[k], h_p[k]);
-    if (has_nl && valid) {
-      const int q = own_xy + zp;
-      ne0 = p_off[q];
-      ne1 = p_off[q + 1];
-      ne2 = p_off[q + 2];
-    }
-  };
-  auto proj = [&](cpx<T> a, int e0, int e1) -> cpx<T> {
-    for (int e = e0; e < e1; e += 2) {
-      const bool two = e + 1 < e1;
-      const int g0 = p_grp[e];
-      const int g1 = two ? p_grp[e + 1] : g0;
-      T ch0[kProjChunk], ch1[kProjChunk];
-      load_chi4(p_chi + kProjChunk * e, ch0);
-      if (two) load_chi4(p_chi + kProjChunk * (e + 1), ch1);
-      const cpx<T>* cg0 = cd + kProjChunk * g0;
-      const cpx<T>* cg1 = cd + kProjChunk * g1;
-#pragma unroll
-      for (int l = 0; l < kProjChunk; ++l) {
-        a = caxpy_r(a, ch0[l], cg0[l]);
-        if (two) a = caxpy_r(a, ch1[l], cg1[l]);
-      }
-    }
-    return a;
   };
   if (z0 < z1) prefetch(z0);
   using A = dacc_t<T>;
@@ -236,7 +199,6 @@ __global__ void __launch_bounds__(kX2Threads, ZM == kZRing1 ? 3 : 2)
 #pragma unroll
     for (int k = 0; k < HPT; ++k)
       if (halo_slot[k] >= 0) pl[bo + halo_slot[k]] = comb(h_r[k], h_p[k]);
-    const int e0 = ne0, e1 = ne1, e2 = ne2;
     if (z + 1 < z1) prefetch(z + 1);  // in flight while this plane is computed
     __syncthreads();
     if (valid) {
@@ -275,8 +237,6 @@ __global__ void __launch_bounds__(kX2Threads, ZM == kZRing1 ? 3 : 2)
           a1 = caxpy_r(a1, st.cz[m], cadd(zb[R - m], zb[R + m]));
         }
       }
-      a0 = proj(a0, e0, e1);
-      a1 = proj(a1, e1, e2);
       st4(w + q, a0, a1);
       st4(pn + q, c, d);
       acc_re += (A)c.re * a0.re - (A)c.im * a0.im + (A)d.re * a1.re - (A)d.im * a1.im;
@@ -303,29 +263,12 @@ __global__ void __launch_bounds__(kX2Threads, ZM == kZRing1 ? 3 : 2)
 
 template <int R, int ZM>
 void launch_zm(const CocgView<float>& cv, const FusedBufs<float>& fb, cudaStream_t s) {
-  constexpr int XO = R + (R & 1);
-  constexpr size_t kPlanes = (ZM == kZRing1 ? 1 : 2) * sizeof(cpx<float>) * (kX2TX + 2 * XO) *
-                             (kX2TY + 2 * R);
-  size_t cdb = fb.cd_in_smem ? sizeof(cpx<float>) * cv.nl.ngroup * kProjChunk : 0;
-  if (ZM == kZRegs) {
-    if (cdb + kPlanes + 1024 > 48 * 1024) cdb = 0;  // static + dynamic within 48 KB
-  } else if (cdb > 8 * 1024) {
-    cdb = 0;  // the ring forms stage at most 8 KB of coefficients next to the ring
-  }
-  const int ring_off = (int)((cdb + 15) / 16 * 16);
-  const size_t dyn = ZM == kZRegs ? cdb : ring_off + x2_ring_bytes<R>();
+  const size_t dyn = ZM == kZRegs ? 0 : x2_ring_bytes<R>();
   const dim3 grid(fb.ntiles_xy, fb.nact, fb.nzchunk);
-  if (fb.first) {
-    if (cdb)
-      k_dirmatvec_x2<R, true, true, ZM><<<grid, kX2Threads, dyn, s>>>(cv, fb, ring_off);
-    else
-      k_dirmatvec_x2<R, true, false, ZM><<<grid, kX2Threads, dyn, s>>>(cv, fb, ring_off);
-  } else {
-    if (cdb)
-      k_dirmatvec_x2<R, false, true, ZM><<<grid, kX2Threads, dyn, s>>>(cv, fb, ring_off);
-    else
-      k_dirmatvec_x2<R, false, false, ZM><<<grid, kX2Threads, dyn, s>>>(cv, fb, ring_off);
-  }
+  if (fb.first)
+    k_dirmatvec_x2<R, true, ZM><<<grid, kX2Threads, dyn, s>>>(cv, fb);
+  else
+    k_dirmatvec_x2<R, false, ZM><<<grid, kX2Threads, dyn, s>>>(cv, fb);
 }
 
 template <int R>
@@ -351,16 +294,10 @@ cudaError_t x2_attr() {
   constexpr int kMax = 96 * 1024;
 #define RPA_X2_ATTR(RR, ZZ)                                                                   \
   if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(k_dirmatvec_x2<RR, true, true, ZZ>,                             \
+    e = cudaFuncSetAttribute(k_dirmatvec_x2<RR, true, ZZ>,                                   \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);             \
   if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(k_dirmatvec_x2<RR, true, false, ZZ>,                            \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);             \
-  if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(k_dirmatvec_x2<RR, false, true, ZZ>,                            \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);             \
-  if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(k_dirmatvec_x2<RR, false, false, ZZ>,                           \
+    e = cudaFuncSetAttribute(k_dirmatvec_x2<RR, false, ZZ>,                                  \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kMax);
 #define RPA_X2_ATTR_R(RR) RPA_X2_ATTR(RR, kZRing1) RPA_X2_ATTR(RR, kZRing2)
   RPA_X2_ATTR_R(1) RPA_X2_ATTR_R(2) RPA_X2_ATTR_R(3) RPA_X2_ATTR_R(4)

@@ -34,7 +34,7 @@ __device__ __forceinline__ void st4(cpx<float>* p, const cpx<float>& a, const cp
 
 __host__ __device__ constexpr int p_rows(int nx) { return kPThreads / (nx / 2); }
 
-template <bool FIRST, bool SMEM_CD, int TY>
+template <bool FIRST, int TY>
 __global__ void __launch_bounds__(kPThreads, 2)
     k_dirmatvec_x2p(CocgView<float> cv, FusedBufs<float> fb) {
   using T = float;
@@ -45,7 +45,6 @@ __global__ void __launch_bounds__(kPThreads, 2)
   constexpr int EXN = kPMaxX + 2 * XO, EYN = TY + 2 * R;
   constexpr int PLN = EXN * EYN;
   __shared__ __align__(16) cpx<T> pl[2 * PLN];
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
   const Stencil<T>& st = cv.st;
   const int nx = st.nx, ny = st.ny, nz = st.nz;
   const int plane = nx * ny;
@@ -67,13 +66,6 @@ __global__ void __launch_bounds__(kPThreads, 2)
   const cpx<T> be = mk<T>((T)sd[kBeta], (T)sd[kBeta + 1]);
   const int b = s / cv.ns, n = s - b * cv.ns;
   const cpx<T> sigma = mk<T>((T)cv.eps[n], (T)cv.omega[b]);
-  const int ncd = cv.nl.ngroup * kProjChunk;
-  const cpx<T>* cd = fb.cp + (long long)s * ncd;
-  if (SMEM_CD) {
-    cpx<T>* scd = reinterpret_cast<cpx<T>*>(dyn_smem);
-    for (int i = threadIdx.x; i < ncd; i += blockDim.x) scd[i] = cd[i];
-    cd = scd;  // read after the first barrier of the z loop
-  }
   // xy offset of the owned pair (its first point; -1 outside a Dirichlet boundary); rows past
   // ny hold the wrapped rows that the last rows of the grid need as y neighbours
   int own_xy = -1;
@@ -153,41 +145,12 @@ __global__ void __launch_bounds__(kPThreads, 2)
     zb[i] = comb(r1, p1);
   }
   cpx<T> nr0, nr1, np0, np1, h_r[kPHpt], h_p[kPHpt];
-  const bool has_nl = cv.nl.ngroup > 0;
-  const int* __restrict__ p_off = cv.nl.p_off;
-  const int* __restrict__ p_grp = cv.nl.p_grp;
-  const T* __restrict__ p_chi = cv.nl.p_chi;
-  int ne0 = 0, ne1 = 0, ne2 = 0;
   auto prefetch = [&](int z) {
     const int zo = zoff(z + R);
     ld2((zo < 0 || own_xy < 0) ? -1 : zo + own_xy, nr0, nr1, np0, np1);
     const int zp = z * plane;
 #pragma unroll
     for (int k = 0; k < kPHpt; ++k) ld1(halo_xy[k] < 0 ? -1 : zp + halo_xy[k], h_r[k], h_p[k]);
-    if (has_nl && valid) {
-      const int q = own_xy + zp;
-      ne0 = p_off[q];
-      ne1 = p_off[q + 1];
-      ne2 = p_off[q + 2];
-    }
-  };
-  auto proj = [&](cpx<T> a, int e0, int e1) -> cpx<T> {
-    for (int e = e0; e < e1; e += 2) {
-      const bool two = e + 1 < e1;
-      const int g0 = p_grp[e];
-      const int g1 = two ? p_grp[e + 1] : g0;
-      T ch0[kProjChunk], ch1[kProjChunk];
-      load_chi4(p_chi + kProjChunk * e, ch0);
-      if (two) load_chi4(p_chi + kProjChunk * (e + 1), ch1);
-      const cpx<T>* cg0 = cd + kProjChunk * g0;
-      const cpx<T>* cg1 = cd + kProjChunk * g1;
-#pragma unroll
-      for (int l = 0; l < kProjChunk; ++l) {
-        a = caxpy_r(a, ch0[l], cg0[l]);
-        if (two) a = caxpy_r(a, ch1[l], cg1[l]);
-      }
-    }
-    return a;
   };
   if (z0 < z1) prefetch(z0);
   using A = dacc_t<T>;
@@ -202,7 +165,6 @@ __global__ void __launch_bounds__(kPThreads, 2)
 #pragma unroll
     for (int k = 0; k < kPHpt; ++k)
       if (halo_slot[k] >= 0) pl[bo + halo_slot[k]] = comb(h_r[k], h_p[k]);
-    const int e0 = ne0, e1 = ne1, e2 = ne2;
     if (z + 1 < z1) prefetch(z + 1);  // in flight while this plane is computed
     __syncthreads();
     if (valid) {
@@ -231,8 +193,6 @@ __global__ void __launch_bounds__(kPThreads, 2)
         a0 = caxpy_r(a0, st.cz[m], cadd(za[R - m], za[R + m]));
         a1 = caxpy_r(a1, st.cz[m], cadd(zb[R - m], zb[R + m]));
       }
-      a0 = proj(a0, e0, e1);
-      a1 = proj(a1, e1, e2);
       st4(w + q, a0, a1);
       st4(pn + q, c, d);
       acc_re += (A)c.re * a0.re - (A)c.im * a0.im + (A)d.re * a1.re - (A)d.im * a1.im;
@@ -257,22 +217,11 @@ __global__ void __launch_bounds__(kPThreads, 2)
 
 template <int TY>
 void launch_ty(const CocgView<float>& cv, const FusedBufs<float>& fb, cudaStream_t s) {
-  constexpr int XO = kPR + (kPR & 1);
-  constexpr size_t kPlanes = 2 * sizeof(cpx<float>) * (kPMaxX + 2 * XO) * (TY + 2 * kPR);
-  size_t cdb = fb.cd_in_smem ? sizeof(cpx<float>) * cv.nl.ngroup * kProjChunk : 0;
-  if (cdb + kPlanes + 1024 > 48 * 1024) cdb = 0;  // static + dynamic within 48 KB
   const dim3 grid(fb.ntiles_xy, fb.nact, fb.nzchunk);
-  if (fb.first) {
-    if (cdb)
-      k_dirmatvec_x2p<true, true, TY><<<grid, kPThreads, cdb, s>>>(cv, fb);
-    else
-      k_dirmatvec_x2p<true, false, TY><<<grid, kPThreads, 0, s>>>(cv, fb);
-  } else {
-    if (cdb)
-      k_dirmatvec_x2p<false, true, TY><<<grid, kPThreads, cdb, s>>>(cv, fb);
-    else
-      k_dirmatvec_x2p<false, false, TY><<<grid, kPThreads, 0, s>>>(cv, fb);
-  }
+  if (fb.first)
+    k_dirmatvec_x2p<true, TY><<<grid, kPThreads, 0, s>>>(cv, fb);
+  else
+    k_dirmatvec_x2p<false, TY><<<grid, kPThreads, 0, s>>>(cv, fb);
 }
 
 }  // namespace

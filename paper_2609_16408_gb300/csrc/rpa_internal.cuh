@@ -67,6 +67,12 @@ struct NonlocalDev {
   const int* p_off;      // N_d + 1, point-major entry offsets
   const int* p_grp;      // group per point-major entry
   const T* p_chi;        // 4 values per point-major entry
+  // overlaps of the projectors of groups with common support, S[g, h](l, m) = sum over the
+  // common points of chi_{g,l} chi_{h,m}: for group g the groups s_nbr[s_off[g] ..
+  // s_off[g + 1]) (g itself included) with one 4 x 4 block each (row-major) in s_blk
+  const int* s_off;
+  const int* s_nbr;
+  const T* s_blk;
 };
 
 // ---------------------------------------------------------------------------------------

@@ -189,9 +189,11 @@ def test_graph_replay_matches_direct_launches(prec):
         assert abs(ref[1] - out[key][1]) <= rt * abs(ref[1]), key
         st = out[key][2]
         assert abs(st["cocg_iters"] - ref[2]["cocg_iters"]) <= 0.02 * ref[2]["cocg_iters"], key
-        # the loops launched on the device are counted like the host-launched ones (the
-        # device loop replays whole chunks, so it may run a few more iterations' launches)
-        assert 0.5 * ref[3] <= out[key][3] <= 2.0 * ref[3], (key, out[key][3], ref[3])
+        # the loops launched on the device are counted like the host-replayed chunk graphs
+        # (the device loop replays whole chunks, so it may run a few more iterations'
+        # launches)
+        lr = out[1, 1][3]
+        assert 0.5 * lr <= out[key][3] <= 2.0 * lr, (key, out[key][3], lr)
     for key in ((0, 1), (1, 1), (2, 1)):
         st = out[key][2]
         assert st["kernel_seconds"][1] > 0 and st["kernel_launches"][1] > 0, key
