@@ -355,6 +355,7 @@ __global__ void __launch_bounds__(kProjNextThreads)
       }
       q[j] = csub(q[j], cmul(al, mk<T>(nl.coef[j] * v.re, nl.coef[j] * v.im)));
     }
+    if (!stage) __syncthreads();  // every read of the old coefficients in place is done
   }
   double dre = 0.0, dim = 0.0;
   for (int j = threadIdx.x; j < nv; j += blockDim.x) {
